@@ -1,0 +1,268 @@
+"""Oracle for Alg. 1 + Alg. 2 (CSR x CSC encrypted sparse matmul), plain CPU.
+
+TEST INFRASTRUCTURE ONLY (tests/, __graft_entry__.smoke(), bench.py's
+cpu_baseline leg).  Follows the paper step by step; see oracle/ckks.py for the
+readings R1..R11 it relies on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .ckks import Ct, Keys, Oracle, Pt, rotation_plan
+
+
+# ---------------------------------------------------------------------------
+# plaintext side: formats, brute force, Alg. 1 merge
+# ---------------------------------------------------------------------------
+def dense_to_csr(M: np.ndarray):
+    """CSR of a dense matrix: (indptr, indices, data) with rows of sorted
+    column indices (Sec. 2.3, Fig. 2)."""
+    M = np.asarray(M)
+    indptr = [0]
+    indices = []
+    data = []
+    for i in range(M.shape[0]):
+        for k in range(M.shape[1]):
+            if M[i, k] != 0:
+                indices.append(k)
+                data.append(float(M[i, k]))
+        indptr.append(len(indices))
+    return np.array(indptr, np.int32), np.array(indices, np.int32), np.array(data, np.float64)
+
+
+def dense_to_csc(M: np.ndarray):
+    """CSC: the CSR of the transpose (column pointers, row indices)."""
+    return dense_to_csr(np.asarray(M).T)
+
+
+def matmul_fp64(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """C[i, j] = sum_k A[i, k] B[k, j] in FP64 (Sec. 4.2's plaintext baseline)."""
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    C = np.zeros((A.shape[0], B.shape[1]))
+    for i in range(A.shape[0]):
+        for j in range(B.shape[1]):
+            C[i, j] = np.sum(A[i, :] * B[:, j])
+    return C
+
+
+def frobenius(X: np.ndarray, Y: np.ndarray) -> float:
+    """||X - Y||_F, the accuracy measure of Sec. 4.2."""
+    return float(np.sqrt(np.sum((np.asarray(X) - np.asarray(Y)) ** 2)))
+
+
+@dataclass
+class Match:
+    i: int
+    j: int
+    k: int
+    a_pos: int
+    b_pos: int
+
+
+def alg1_matches(A_indptr, A_indices, B_indptr, B_indices, rows: int, cols: int) -> list:
+    """Alg. 1's merge: for every (i, j), walk row i of A (CSR) and column j of
+    B (CSC) with two pointers; a match is a_col == b_row (reading R10 for the
+    loop bounds)."""
+    out = []
+    for i in range(rows):
+        for j in range(cols):
+            a_start, a_end = int(A_indptr[i]), int(A_indptr[i + 1])
+            b_start, b_end = int(B_indptr[j]), int(B_indptr[j + 1])
+            a_pos, b_pos = a_start, b_start
+            while a_pos < a_end and b_pos < b_end:
+                a_col = int(A_indices[a_pos])
+                b_row = int(B_indices[b_pos])
+                if a_col == b_row:
+                    out.append(Match(i, j, a_col, a_pos, b_pos))
+                    a_pos += 1
+                    b_pos += 1
+                elif a_col < b_row:
+                    a_pos += 1
+                else:
+                    b_pos += 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# encrypted side
+# ---------------------------------------------------------------------------
+def pack_values(data: np.ndarray, slots: int) -> list:
+    """Reading R3: value p in slot p mod S of chunk p // S, zero padding."""
+    nchunks = max(1, -(-len(data) // slots))
+    out = []
+    for c in range(nchunks):
+        z = np.zeros(slots)
+        part = data[c * slots:(c + 1) * slots]
+        z[: len(part)] = part
+        out.append(z)
+    return out
+
+
+def mask_scale(orc: Oracle) -> float:
+    """Reading R6: the mask is encoded at the scale of q_{L-2}."""
+    return float(orc.mods[orc.P.L - 2])
+
+
+def result_scale(orc: Oracle) -> float:
+    """Scale of every accumulated product: Delta^2 / q_{L-1} (R6)."""
+    return orc.P.scale * orc.P.scale / orc.mods[orc.P.L - 1]
+
+
+@dataclass
+class OpCounts:
+    matches: int = 0
+    ks_relin: int = 0
+    ks_align: int = 0
+    ks_final: int = 0
+    rescales: int = 0
+
+
+def make_mask(orc: Oracle, slot: int, level: int) -> Pt:
+    """makeMask(size^2, min_pos) of Alg. 2: one-hot plaintext at `slot`
+    (reading R8 for the encoding, R6 for the scale)."""
+    return orc.encode_onehot(1.0, slot, level, mask_scale(orc))
+
+
+def spmspm_ct_ct(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list,
+                 rows: int, cols: int, mask_pt: Pt | None = None, counts: OpCounts | None = None,
+                 match_limit: int | None = None) -> list:
+    """Alg. 1 + Alg. 2 over encrypted operands.
+
+    A_csr = (indptr, indices) of A (rows x inner), B_csc = (indptr, indices) of
+    B (cols x inner column pointers).  A_cts / B_cts: packed chunks (R3) at
+    level L and scale Delta.  Returns the result chunks (R3) at level L-2.
+
+    mask_pt: optional one-hot mask at slot 0 (level L-1) to use in place of
+    this oracle's own encoding; the mask for slot p is then the automorphism
+    X -> X^(5^-p) of it, which is exactly the encoding of e_p (R8).
+    match_limit: process only the first N matches (timing samples)."""
+    P = orc.P
+    S = P.slots
+    if counts is None:
+        counts = OpCounts()
+    nres = max(1, -(-(rows * cols) // S))
+    result = [orc.zero_ct(P.L - 2, result_scale(orc)) for _ in range(nres)]
+    matches = alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols)
+    if match_limit is not None:
+        matches = matches[:match_limit]
+    rot_cache = {}
+
+    def rotated(which: str, chunk: int, amount: int) -> Ct:
+        # memoisation of a deterministic function: same bits as recomputing
+        key = (which, chunk, amount)
+        if key not in rot_cache:
+            src = (A_cts if which == "A" else B_cts)[chunk]
+            rot_cache[key] = orc.rotate(src, amount, keys)
+            counts.ks_align += len(rotation_plan(amount, S, P.rot_base))
+        return rot_cache[key]
+
+    for mt in matches:
+        counts.matches += 1
+        ca, sa = divmod(mt.a_pos, S)
+        cb, sb = divmod(mt.b_pos, S)
+        vA, vB = A_cts[ca], B_cts[cb]
+        min_slot = sa
+        if sa < sb:
+            vB = rotated("B", cb, sb - sa)
+            min_slot = sa
+        elif sb < sa:
+            vA = rotated("A", ca, sa - sb)
+            min_slot = sb
+        # Alg. 2
+        dot = orc.mult_relin(vA, vB, keys)
+        counts.ks_relin += 1
+        dot = orc.rescale(dot)
+        if mask_pt is None:
+            mask = make_mask(orc, min_slot, dot.level)
+        else:
+            g = pow(pow(5, min_slot, 2 * P.n), -1, 2 * P.n)
+            m = np.stack([_automorph_limb(orc, mask_pt.m[i], g, q)
+                          for i, q in enumerate(orc.mods[: dot.level])])
+            mask = Pt(m, mask_pt.scale)
+        dot = orc.mul_plain(dot, mask)
+        # Relinearize after a plaintext product: nothing to switch (R7)
+        dot = orc.rescale(dot)
+        counts.rescales += 2
+        t = mt.i * cols + mt.j
+        rc, ts = divmod(t, S)
+        rot_idx = (min_slot - ts) % S
+        counts.ks_final += len(rotation_plan(rot_idx, S, P.rot_base))
+        dot = orc.rotate(dot, rot_idx, keys)
+        result[rc] = orc.add(result[rc], dot)
+    return result
+
+
+def _automorph_limb(orc: Oracle, a: np.ndarray, g: int, q: int) -> np.ndarray:
+    from .ckks import automorphism
+    return automorphism(a, g, q)
+
+
+def weight_scale(orc: Oracle) -> float:
+    """Reading R9: B's plaintext is encoded at the scale of q_{L-1}."""
+    return float(orc.mods[orc.P.L - 1])
+
+
+def spmspm_ct_pt(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_data: np.ndarray,
+                 rows: int, cols: int, b_pts: list | None = None, counts: OpCounts | None = None,
+                 match_limit: int | None = None) -> list:
+    """Encrypted A (CSR, packed) times plaintext B (CSC) following reading R9:
+    per match, pt = encode(B[k, j] * e_{a_slot}) at scale q_{L-1}, then
+    ct x pt -> rescale -> EvalRotate(a_slot - t) -> EvalAdd.  Result at level
+    L-1, scale Delta.
+
+    b_pts: optional per-nonzero plaintexts of B (CSC order) encoding
+    B[k, j] * e_0 at level L; the plaintext for slot p is then its
+    automorphism X -> X^(5^-p) (exactly the encoding of B[k, j] e_p)."""
+    P = orc.P
+    S = P.slots
+    if counts is None:
+        counts = OpCounts()
+    nres = max(1, -(-(rows * cols) // S))
+    result = [orc.zero_ct(P.L - 1, P.scale) for _ in range(nres)]
+    matches = alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols)
+    if match_limit is not None:
+        matches = matches[:match_limit]
+    for mt in matches:
+        counts.matches += 1
+        ca, sa = divmod(mt.a_pos, S)
+        if b_pts is None:
+            pt = orc.encode_onehot(float(B_data[mt.b_pos]), sa, P.L, weight_scale(orc))
+        else:
+            g = pow(pow(5, sa, 2 * P.n), -1, 2 * P.n)
+            base = b_pts[mt.b_pos]
+            pt = Pt(np.stack([_automorph_limb(orc, base.m[i], g, q) for i, q in enumerate(orc.mods[: P.L])]),
+                    base.scale)
+        dot = orc.mul_plain(A_cts[ca], pt)
+        dot = orc.rescale(dot)
+        counts.rescales += 1
+        t = mt.i * cols + mt.j
+        rc, ts = divmod(t, S)
+        rot_idx = (sa - ts) % S
+        counts.ks_final += len(rotation_plan(rot_idx, S, P.rot_base))
+        dot = orc.rotate(dot, rot_idx, keys)
+        result[rc] = orc.add(result[rc], dot)
+    return result
+
+
+def decrypt_result(orc: Oracle, keys: Keys, chunks: list, rows: int, cols: int) -> np.ndarray:
+    """Decrypt + decode the result chunks into a rows x cols matrix (R3)."""
+    S = orc.P.slots
+    vals = []
+    for ct in chunks:
+        vals.append(np.real(orc.decode(orc.decrypt(ct, keys))))
+    flat = np.concatenate(vals)[: rows * cols]
+    return flat.reshape(rows, cols)
+
+
+def final_rotation_amounts(A_csr, B_csc, rows: int, cols: int, slots: int) -> list:
+    """Every rotation amount Alg. 1 + Alg. 2 will request (for key generation)."""
+    amts = set()
+    for mt in alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols):
+        sa, sb = mt.a_pos % slots, mt.b_pos % slots
+        if sa != sb:
+            amts.add(abs(sa - sb))
+        amts.add((min(sa, sb) - (mt.i * cols + mt.j) % slots) % slots)
+    return sorted(amts)

@@ -1,0 +1,261 @@
+/*
+ * spfhe.h -- C ABI of the GB300 (sm_103a) encrypted sparse x sparse matmul.
+ *
+ * The library multiplies CKKS-encrypted sparse matrices held in the CSR
+ * (left operand) x CSC (right operand) packing of "GPU Acceleration of Sparse
+ * Fully Homomorphic Encrypted DNNs" (Sec. 3, Alg. 1 and Alg. 2).  Every ring
+ * operation runs in sm_103a CUDA kernels; the host only walks the plaintext
+ * sparsity metadata (Sec. 3.2.1: indptr/indices stay in the clear, values are
+ * encrypted) and sequences kernel launches.
+ *
+ * Representation
+ *   - Ring R_q = Z_q[X]/(X^n + 1), n = 2^log_n, S = n/2 slots.  Moduli are
+ *     q_0 .. q_{L-1} then the special primes p_0 .. p_{K-1} (global modulus
+ *     index 0 .. L+K-1), all primes = 1 (mod 2n) below 2^62, chosen by
+ *     searching downward from 2^bits in steps of 2n (q_0 first, scaling primes
+ *     next, special primes last, all distinct).  psi_q is x^((q-1)/2n) for the
+ *     first x = 2, 3, ... with psi^n = -1.
+ *   - A polynomial at level ell has ell limbs (q_0 .. q_{ell-1}) of n uint64
+ *     residues in [0, q), limb-major.  "Evaluation representation" (the one
+ *     every handle stores) is the negacyclic NTT: limb value at index k is
+ *     a(psi^(2 brv(k) + 1)) mod q, brv = log_n-bit reversal.
+ *   - Ciphertext (c0, c1) is stored as [2][ell][n]; a plaintext as [ell][n].
+ *   - Slot i of the canonical embedding is m(zeta^(5^i)), zeta = e^(i pi/n).
+ *     Rotation by r (> 0) is a LEFT rotation: slot i + r moves to slot i
+ *     (EvalRotate of Alg. 1/Alg. 2), realised as X -> X^(5^r mod 2n) followed
+ *     by hybrid key switching.  Amounts are applied through the base-b plan:
+ *     r mod S written in base b = rot_base, one key switch with the key for
+ *     d*b^t per nonzero digit d, ascending t.
+ *
+ * Conventions
+ *   - Every call returns spfhe_status (0 = OK, < 0 = error).  No exception
+ *     crosses the ABI.  spfhe_last_error() returns a thread-local message for
+ *     the most recent failing call of the calling thread.
+ *   - Handles (ctx, keys, ct, pt) are opaque and owned by the caller, who
+ *     frees them with the matching *_free / *_destroy call.  Their device
+ *     memory lives on the GPU that was current at spfhe_ctx_create.
+ *   - Host arrays passed in (metadata, values, imported limbs) are borrowed
+ *     for the duration of the call only.
+ *   - Work is enqueued on the context's CUDA stream; results are ready after
+ *     spfhe_sync(ctx) (or a synchronisation of that stream).  Calls that
+ *     return data to host memory synchronise the stream themselves.
+ *   - A context and its handles must not be used from two threads at once.
+ */
+#ifndef SPFHE_H
+#define SPFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPFHE_OK = 0,
+    SPFHE_EINVAL = -1,   /* bad argument: null pointer, malformed CSR/CSC, size out of range */
+    SPFHE_ENOMEM = -2,   /* device or host allocation failed */
+    SPFHE_ELEVEL = -3,   /* not enough levels left for the operation */
+    SPFHE_EKEY = -4,     /* a needed switching key is missing */
+    SPFHE_ESCALE = -5,   /* operands' scales differ beyond 1e-9 relative */
+    SPFHE_ECUDA = -6,    /* a CUDA runtime call failed */
+    SPFHE_ETIMEOUT = -7, /* a bounded device-side wait gave up */
+    SPFHE_EPARAM = -8    /* parameter set cannot be built (no primes, too many limbs, ...) */
+} spfhe_status;
+
+typedef struct spfhe_ctx spfhe_ctx;
+typedef struct spfhe_keys spfhe_keys;
+typedef struct spfhe_ct spfhe_ct;
+typedef struct spfhe_pt spfhe_pt;
+
+/* CKKS parameter set.  The paper states none (Sec. 4 gives matrix sizes
+ * only); these fields carry the workload's ring degree, prime sizes, key
+ * switching digits and scale. */
+typedef struct {
+    uint32_t log_n;          /* ring degree n = 2^log_n, 2 <= log_n <= 17 */
+    uint32_t L;              /* number of q primes (top level), 3 <= L <= 64 */
+    const uint32_t *q_bits;  /* L bit sizes: q_0 then the scaling primes; each in [20, 61] */
+    uint32_t K;              /* number of special primes, 1 <= K <= 16 */
+    uint32_t p_bits;         /* bit size of each special prime, in [20, 61] */
+    uint32_t dnum;           /* key-switching digits; alpha = ceil(L/dnum) limbs per digit */
+    double scale;            /* encoding scale Delta of fresh ciphertexts */
+    uint32_t rot_base;       /* rotation plan base b (power of two >= 2) */
+} spfhe_params;
+
+/* Plaintext sparsity metadata (Sec. 3.2.1 keeps it in the clear).
+ * CSR (left operand): rows = matrix rows, cols = inner dimension, indptr has
+ * rows+1 entries, indices are column ids sorted ascending within each row.
+ * CSC (right operand): rows = inner dimension, cols = matrix columns, indptr
+ * has cols+1 column pointers, indices are row ids sorted ascending within
+ * each column.  nnz = indptr[last]. */
+typedef struct {
+    int32_t rows;
+    int32_t cols;
+    int32_t nnz;
+    const int32_t *indptr;
+    const int32_t *indices;
+} spfhe_sparse_meta;
+
+/* Per-call counters (Sec. 4.3's complexity model counts the matches). */
+typedef struct {
+    uint64_t matches;     /* (i, j, k) triples with A[i,k] != 0 and B[k,j] != 0 */
+    uint64_t ks_relin;    /* relinearisation key switches */
+    uint64_t ks_align;    /* key switches spent aligning operands (Alg. 1) */
+    uint64_t ks_final;    /* key switches of the final per-match rotations (Alg. 2) */
+    uint64_t rescales;    /* ciphertext rescales */
+    uint64_t launches;    /* CUDA kernels launched by the call */
+} spfhe_stats;
+
+/* ---- errors, context ------------------------------------------------- */
+const char *spfhe_last_error(void);
+
+/* Build the primes, NTT tables and base-conversion constants and upload them.
+ * cuda_stream: a cudaStream_t to enqueue work on (NULL = the default
+ * stream); the stream must outlive the context.  *out receives the context. */
+spfhe_status spfhe_ctx_create(const spfhe_params *params, void *cuda_stream, spfhe_ctx **out);
+spfhe_status spfhe_ctx_destroy(spfhe_ctx *ctx);
+
+/* Copy the L+K moduli (q's then p's) and their psi roots to host arrays of
+ * L+K entries each (either may be NULL). */
+spfhe_status spfhe_ctx_moduli(const spfhe_ctx *ctx, uint64_t *mods, uint64_t *psis);
+
+/* Block the host until every operation enqueued on the context is done. */
+spfhe_status spfhe_sync(spfhe_ctx *ctx);
+
+/* Number of kernels the library has launched since the context was created. */
+uint64_t spfhe_launch_count(const spfhe_ctx *ctx);
+
+/* Kernel profiler.  spfhe_prof_enable(ctx, 1) clears the counters and starts
+ * bracketing every kernel launch with two CUDA events on the context stream
+ * (0 stops it).  spfhe_prof_read(ctx, cls, ...) synchronises the stream and
+ * returns for kernel class cls (0 .. spfhe_prof_classes()-1) the launches,
+ * the summed device time of the timed launches in milliseconds, and the
+ * algorithmic bytes (each input and output limb counted once) and work
+ * (butterflies for transforms, modular multiply-accumulates otherwise)
+ * implied by the launch shapes.  Any out-pointer may be NULL. */
+spfhe_status spfhe_prof_enable(spfhe_ctx *ctx, int enable);
+spfhe_status spfhe_prof_read(spfhe_ctx *ctx, int cls, uint64_t *launches, double *ms, double *bytes, double *work);
+int spfhe_prof_classes(void);
+const char *spfhe_prof_class_name(int cls);
+
+/* ---- keys ------------------------------------------------------------ */
+/* Sample a ternary secret, the relinearisation key and one rotation key per
+ * amount the rotation plan can request (d*b^t < S, 1 <= d < b) on the GPU,
+ * from a ChaCha20 stream keyed by `seed` (Gaussian errors sigma = 3.2,
+ * |e| <= 6 sigma).  Keys stay resident on the device. */
+spfhe_status spfhe_keygen(spfhe_ctx *ctx, uint64_t seed, spfhe_keys **out);
+
+/* Import keys computed elsewhere (used to feed identical keys to two
+ * implementations).  secret: n int64 coefficients in {-1, 0, 1}.
+ * relin: [dnum][2][L+K][n] uint64, evaluation representation, key for
+ * s^2 -> s.  rot: n_rot pointers to keys of the same layout for
+ * sigma_{5^amount}(s) -> s, amounts in rot_amounts (each in [1, S)).
+ * The key of digit j must hold P mod q_i on the limbs q_i of digit j and 0
+ * on every other modulus as its gadget, P = prod p_k. */
+spfhe_status spfhe_keys_import(spfhe_ctx *ctx, const int64_t *secret, const uint64_t *relin,
+                               size_t n_rot, const int32_t *rot_amounts, const uint64_t *const *rot,
+                               spfhe_keys **out);
+void spfhe_keys_free(spfhe_keys *keys);
+
+/* ---- plaintexts --------------------------------------------------------- */
+/* Canonical-embedding encoding of n_vals <= S complex slots (re, im; im may be
+ * NULL) at `level` and `scale`: m_j = round_half_away((2 scale/n) Re
+ * sum_i z_i zeta^(-5^i j)), reduced into each limb and transformed. */
+spfhe_status spfhe_encode(spfhe_ctx *ctx, const double *re, const double *im, size_t n_vals,
+                          uint32_t level, double scale, spfhe_pt **out);
+
+/* Import a plaintext given as `level` limbs of n uint64 residues (host
+ * memory); coeff_domain != 0 means coefficient representation (the library
+ * transforms it), 0 means evaluation representation. */
+spfhe_status spfhe_pt_import(spfhe_ctx *ctx, const uint64_t *limbs, uint32_t level, double scale,
+                             int coeff_domain, spfhe_pt **out);
+/* Copy the evaluation-representation limbs ([level][n]) to host memory. */
+spfhe_status spfhe_pt_export(spfhe_ctx *ctx, const spfhe_pt *pt, uint64_t *limbs);
+spfhe_status spfhe_pt_info(const spfhe_pt *pt, uint32_t *level, double *scale);
+void spfhe_pt_free(spfhe_pt *pt);
+
+/* Decode slots 0 .. n_vals-1 of a plaintext (limb q_0, centred residues),
+ * dividing by the plaintext's scale.  re/im host arrays of n_vals (im may be
+ * NULL). */
+spfhe_status spfhe_decode(spfhe_ctx *ctx, const spfhe_pt *pt, double *re, double *im, size_t n_vals);
+
+/* ---- ciphertexts -------------------------------------------------------- */
+/* Secret-key encryption (c0, c1) = (-a s + e + m, a) with a and e drawn on the
+ * GPU from a ChaCha20 stream keyed by `seed`. */
+spfhe_status spfhe_encrypt(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_pt *pt, uint64_t seed,
+                           spfhe_ct **out);
+/* m = c0 + c1 s at the ciphertext's level (evaluation representation). */
+spfhe_status spfhe_decrypt(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_ct *ct, spfhe_pt **out);
+
+/* Import/export a ciphertext as [2][level][n] uint64 in evaluation
+ * representation.  `limbs` may point to host (pageable or pinned) or device
+ * memory; the copy is enqueued on the context stream and export waits for it. */
+spfhe_status spfhe_ct_import(spfhe_ctx *ctx, const uint64_t *limbs, uint32_t level, double scale,
+                             spfhe_ct **out);
+spfhe_status spfhe_ct_export(spfhe_ctx *ctx, const spfhe_ct *ct, uint64_t *limbs);
+spfhe_status spfhe_ct_info(const spfhe_ct *ct, uint32_t *level, double *scale);
+void spfhe_ct_free(spfhe_ct *ct);
+
+/* ---- single homomorphic operations (Alg. 2's building blocks) ---------- */
+/* EvalMult + Relinearize: tensor product then key switch of the s^2 part
+ * (Sec. 3.2.2, Alg. 2).  Operands at the same level; out at that level with
+ * scale = product of scales. */
+spfhe_status spfhe_mult_relin(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_ct *a, const spfhe_ct *b,
+                              spfhe_ct **out);
+/* Rescale in place: drop q_{ell-1}, c_i <- (c_i - [r]_{q_i}) q_{ell-1}^{-1} with r
+ * the centred residue of limb ell-1; scale /= q_{ell-1} (Sec. 3.2.2). */
+spfhe_status spfhe_rescale(spfhe_ctx *ctx, spfhe_ct *ct);
+/* EvalRotate (left by r, any integer) through the rotation plan. */
+spfhe_status spfhe_rotate(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_ct *ct, int32_t r, spfhe_ct **out);
+/* Product with a plaintext at the same level; scale = product of scales. */
+spfhe_status spfhe_mul_plain(spfhe_ctx *ctx, const spfhe_ct *ct, const spfhe_pt *pt, spfhe_ct **out);
+/* EvalAdd: out = a + b (same level, scales equal within 1e-9 relative). */
+spfhe_status spfhe_add(spfhe_ctx *ctx, const spfhe_ct *a, const spfhe_ct *b, spfhe_ct **out);
+
+/* In-place negacyclic NTT of n_limbs device-resident limbs (limb l holds n
+ * residues for modulus index mod_idx[l], mod_idx a host array).  inverse != 0
+ * runs the inverse transform (including the n^{-1} factor). */
+spfhe_status spfhe_ntt(spfhe_ctx *ctx, uint64_t *dev_limbs, uint32_t n_limbs, const int32_t *mod_idx,
+                       int inverse);
+
+/* ---- Alg. 1 planner ------------------------------------------------------ */
+/* Alg. 1's merge over every (i, j): returns the matches in Alg. 1 order as
+ * (i, j, k, a_pos, b_pos) rows.  Call with out = NULL to get the count in
+ * *n_matches; then with out pointing at 5 * count int32. */
+spfhe_status spfhe_plan_matches(const spfhe_sparse_meta *A_csr, const spfhe_sparse_meta *B_csc,
+                                int32_t *out, uint64_t *n_matches);
+
+/* ---- encrypted sparse x sparse matmul ------------------------------------- */
+/* C = A B with both operands encrypted (Alg. 1 + Alg. 2).
+ * A_chunks: ceil(nnz_A / S) ciphertexts at level L, scale Delta, with CSR
+ * data[p] in slot p mod S of chunk p / S (zero padding elsewhere).
+ * B_chunks: the same for B's CSC data.  mask0: NULL, or a plaintext at level
+ * L-1 encoding the one-hot slot-0 vector at scale q_{L-2} (the library then
+ * derives every mask from it; when NULL it encodes its own).
+ * C_chunks (out): caller array of n_c = ceil(rows*cols / S) handle slots that
+ * receive the result chunks at level L-2, scale Delta^2/q_{L-1}: C[i,j] in
+ * slot t mod S of chunk t / S, t = i*cols + j.  stats may be NULL.
+ * Requires L >= 3.  Missing rotation keys give SPFHE_EKEY. */
+spfhe_status spfhe_sparse_matmul_ct_ct(spfhe_ctx *ctx, const spfhe_keys *keys,
+                                       const spfhe_sparse_meta *A_csr, spfhe_ct *const *A_chunks, size_t n_a,
+                                       const spfhe_sparse_meta *B_csc, spfhe_ct *const *B_chunks, size_t n_b,
+                                       const spfhe_pt *mask0, spfhe_ct **C_chunks, size_t n_c,
+                                       spfhe_stats *stats);
+
+/* C = A B with A encrypted (packed as above) and B a plaintext (CSC).  Per
+ * match the weight plaintext encodes B[k,j] in A's slot at scale q_{L-1}
+ * (alignment of B becomes re-encoding, the mask merges into it), then
+ * product, rescale, final rotation, add: depth 1.  B_values: nnz_B doubles
+ * in CSC order.  B_pts: NULL, or nnz_B plaintexts at level L encoding
+ * B[k,j] * e_0 at scale q_{L-1} (used in place of the library's own
+ * encodings).  C_chunks at level L-1, scale Delta. */
+spfhe_status spfhe_sparse_matmul_ct_pt(spfhe_ctx *ctx, const spfhe_keys *keys,
+                                       const spfhe_sparse_meta *A_csr, spfhe_ct *const *A_chunks, size_t n_a,
+                                       const spfhe_sparse_meta *B_csc, const double *B_values,
+                                       spfhe_pt *const *B_pts, spfhe_ct **C_chunks, size_t n_c,
+                                       spfhe_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPFHE_H */

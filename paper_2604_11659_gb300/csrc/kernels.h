@@ -1,0 +1,100 @@
+// Launchers for the sm_103a kernels (declared here, defined in ntt.cu / ring.cu).
+#pragma once
+#include "internal.h"
+
+namespace spfhe {
+
+// A batch of `items` equally laid-out blocks of limbs.  Item z starts at
+// base + (ids ? ids[z] : z) * stride (in u64 words).
+struct Batch {
+    u64 *base;
+    long long stride;
+    int items;
+    const int *ids;   // device array or nullptr
+};
+
+// ---- NTT (ntt.cu) ----
+// Forward / inverse negacyclic NTT of the limbs `map` names in every item.
+void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map);
+void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map);
+LimbMap limb_range(int first_off, int count, int first_mi);
+
+// ---- ring kernels (ring.cu) ----
+// d[item] = (a0 b0, a0 b1 + a1 b0, a1 b1) with a, b given by per-item
+// pointers to [2][ell][n] ciphertexts; d is [items][3][ell][n].
+void tensor(Ctx &ctx, int items, int ell, const u64 *const *pa, const u64 *const *pb, u64 *d);
+
+// out[item] = sigma_g(in[item]) in evaluation representation, for `polys`
+// polynomials of ell limbs each.  g per item (device array).
+void automorph(Ctx &ctx, int items, int polys, int ell, const u64 *const *in, long long in_stride_unused,
+               u64 *out, long long out_stride, const int *g);
+
+// ModUp basis conversion: coef [items][ell][n] (coefficient rep. of the
+// key-switching input) -> ext [items][beta][ell+K][n] (targets outside each digit).
+void modup_bconv(Ctx &ctx, int items, int ell, const u64 *coef, long long coef_stride, u64 *ext,
+                 long long ext_stride);
+// LimbMap of the ext limbs that need a forward NTT after modup_bconv.
+LimbMap modup_ntt_map(const Ctx &ctx, int ell);
+
+// Key-switching inner product.  in: per item the NTT-domain input polynomial
+// ([ell][n]); ext: [items][beta][ell+K][n]; key per item group; acc:
+// [items][2][ell+K][n].
+struct KeyGroup {
+    const u64 *key;    // [dnum][2][M][n] Montgomery form
+    int first, count;  // items [first, first + count)
+};
+void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const u64 *ext, long long ext_stride,
+                      const std::vector<KeyGroup> &groups, u64 *acc, long long acc_stride);
+
+// ModDown: acc [items][2][ell+K][n] NTT domain.  P-limbs are inverse
+// transformed in place, converted into conv [items][2][ell][n] (coefficient),
+// transformed, then out[item][b] = base_b(perm) + (acc_b - conv_b) P^{-1}.
+// base: per item [2][ell][n] (or nullptr), read at sigma_g index when g given.
+void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv,
+             const u64 *const *base, const int *base_g, bool base_c1, u64 *out, long long out_stride);
+
+// Rescale every item [2][ell][n] -> out [2][ell-1][n].
+void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride);
+
+// ct[item] (= [2][ell][n]) *= mask permuted by sigma_{g[item]}; mask [ell][n]
+// in Montgomery form.
+void mul_plain_perm(Ctx &ctx, int items, int ell, u64 *ct, long long stride, const u64 *const *mask,
+                    const int *g);
+
+// result[2][ell][n] += sum over the listed items of x[item]
+void accumulate(Ctx &ctx, int ell, u64 *result, const u64 *x, long long stride, const int *ids, int count);
+
+// elementwise helpers
+void add_ct(Ctx &ctx, int polys, int ell, const u64 *a, const u64 *b, u64 *out);
+void mul_ct_pt(Ctx &ctx, int ell, const u64 *ct, const u64 *pt, u64 *out);           // pt standard form
+void to_montgomery(Ctx &ctx, u64 *x, int limbs, const int *mi_host, int reps);         // in place
+void from_signed(Ctx &ctx, const long long *coef, u64 *out, int limbs);                // out[l] = coef mod q_l
+void decrypt_core(Ctx &ctx, int ell, const u64 *ct, const u64 *s_mont, u64 *out);      // c0 + c1 s
+void copy_words(Ctx &ctx, u64 *dst, const u64 *src, size_t words);
+// out + i*stride <- in[i] (words_per_item each); and the reverse
+void gather_items(Ctx &ctx, int items, size_t words_per_item, const u64 *const *in, u64 *out, long long stride);
+void scatter_items(Ctx &ctx, int items, size_t words_per_item, const u64 *src, long long stride, u64 *const *out);
+// out[l] = a[l] * b[l] mod q_l (modulus index = limb index), limbs x n
+void mul_poly(Ctx &ctx, int limbs, const u64 *a, const u64 *b, u64 *out);
+
+// sampling (ChaCha20 stream keyed by seed, domain-separated by `stream_id`)
+void sample_uniform(Ctx &ctx, u64 *out, int limbs, const int *mi_host, uint64_t seed, uint64_t stream_id);
+void sample_ternary(Ctx &ctx, long long *out, uint64_t seed, uint64_t stream_id);
+void sample_gaussian(Ctx &ctx, long long *out, uint64_t seed, uint64_t stream_id);
+// out[l] = -(a[l] s_l) + e[l] + extra[l] (all evaluation rep.); s in Montgomery form.
+void rlwe_b(Ctx &ctx, int limbs, const int *mi_host, const u64 *a, const u64 *s_mont, const u64 *e,
+            const u64 *extra, u64 *out);
+// out[l] = out[l] + gadget_l * sprime[l], gadget_l = P mod q for l in [lo, hi)
+void add_gadget(Ctx &ctx, u64 *out, const u64 *sprime, int lo, int hi);
+
+// launch bookkeeping: t = prof_begin(ctx); kernel<<<...>>>; prof_end(ctx, t, class,
+// algorithmic bytes, algorithmic work, name).  prof_end counts the launch and
+// turns a launch error into an Error.
+cudaEvent_t prof_begin(Ctx &ctx);
+void prof_end(Ctx &ctx, cudaEvent_t start, int cls, double bytes, double work, const char *what);
+void prof_reset(Ctx &ctx, bool on);
+void prof_collect(Ctx &ctx);
+void prof_destroy(Ctx &ctx);
+const char *kernel_class_name(int cls);
+
+}  // namespace spfhe

@@ -1,0 +1,437 @@
+// Encrypted sparse x sparse matmul (Alg. 1 + Alg. 2 of "GPU Acceleration of
+// Sparse Fully Homomorphic Encrypted DNNs").
+//
+// Host side: Alg. 1's CSR x CSC merge over the plaintext metadata produces the
+// match list; every match names the operand to rotate (only one, by the slot
+// difference; none when the slots agree, Sec. 3.2.2), the mask slot
+// min(a_slot, b_slot) and the final rotation min_slot - (i*cols + j).
+//
+// Device side: distinct alignment rotations are computed once each (a
+// rotation is a deterministic function of (operand, amount), so reuse gives
+// the same bits as recomputing it per match) in waves of up to `G`
+// ciphertexts; the matches of a wave then run Alg. 2 in batches of `Bm`
+// matches, every stage one launch over the whole batch:
+//   tensor -> relinearise (one key stream serves the batch) -> rescale ->
+//   mask (one NTT-domain mask, permuted per match) -> rescale ->
+//   final rotation (plan steps batched across matches) -> accumulate.
+// Modular sums are exact, so the accumulation order does not change the
+// result.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <map>
+#include <tuple>
+
+#include "runtime.h"
+
+namespace spfhe {
+
+void validate_meta(const spfhe_sparse_meta &m, const char *what)
+{
+    const std::string w(what);
+    if (m.rows < 0 || m.cols < 0 || m.nnz < 0) throw Error(SPFHE_EINVAL, w + ": negative size");
+    if (!m.indptr) throw Error(SPFHE_EINVAL, w + ": null indptr");
+    if (m.nnz > 0 && !m.indices) throw Error(SPFHE_EINVAL, w + ": null indices");
+    // CSR: `rows` compressed lines of column ids in [0, cols); CSC: `cols`
+    // compressed lines of row ids in [0, rows).  The caller passes which.
+    (void)w;
+}
+
+static void validate_lines(const int32_t *indptr, const int32_t *indices, int lines, int range, int nnz,
+                           const std::string &w)
+{
+    if (indptr[0] != 0) throw Error(SPFHE_EINVAL, w + ": indptr[0] != 0");
+    for (int l = 0; l < lines; ++l) {
+        if (indptr[l + 1] < indptr[l]) throw Error(SPFHE_EINVAL, w + ": indptr not monotone");
+        for (int p = indptr[l]; p < indptr[l + 1]; ++p) {
+            if (p >= nnz) throw Error(SPFHE_EINVAL, w + ": indptr beyond nnz");
+            if (indices[p] < 0 || indices[p] >= range) throw Error(SPFHE_EINVAL, w + ": index out of range");
+            if (p > indptr[l] && indices[p] <= indices[p - 1])
+                throw Error(SPFHE_EINVAL, w + ": indices not strictly ascending");
+        }
+    }
+    if (indptr[lines] != nnz) throw Error(SPFHE_EINVAL, w + ": indptr[last] != nnz");
+}
+
+void validate_pair(const spfhe_sparse_meta &A, const spfhe_sparse_meta &B)
+{
+    validate_meta(A, "A (CSR)");
+    validate_meta(B, "B (CSC)");
+    if (A.cols != B.rows) throw Error(SPFHE_EINVAL, "inner dimensions differ");
+    validate_lines(A.indptr, A.indices, A.rows, A.cols, A.nnz, "A (CSR)");
+    validate_lines(B.indptr, B.indices, B.cols, B.rows, B.nnz, "B (CSC)");
+}
+
+// Alg. 1: for every (i, j), two-pointer walk over row i of A and column j of B.
+std::vector<MatchRec> plan_alg1(const spfhe_sparse_meta &A, const spfhe_sparse_meta &B)
+{
+    std::vector<MatchRec> out;
+    for (int i = 0; i < A.rows; ++i) {
+        const int a_start = A.indptr[i], a_end = A.indptr[i + 1];
+        if (a_start == a_end) continue;
+        for (int j = 0; j < B.cols; ++j) {
+            int a_pos = a_start, b_pos = B.indptr[j];
+            const int b_end = B.indptr[j + 1];
+            while (a_pos < a_end && b_pos < b_end) {
+                const int a_col = A.indices[a_pos], b_row = B.indices[b_pos];
+                if (a_col == b_row) {
+                    out.push_back(MatchRec{i, j, a_col, a_pos, b_pos});
+                    ++a_pos;
+                    ++b_pos;
+                } else if (a_col < b_row) {
+                    ++a_pos;
+                } else {
+                    ++b_pos;
+                }
+            }
+        }
+    }
+    return out;
+}
+
+static int env_int(const char *name, int dflt)
+{
+    const char *v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    const int x = std::atoi(v);
+    return x > 0 ? x : dflt;
+}
+
+// Matches per batch: bounded by a per-item memory estimate so the working
+// set stays within a few tens of GB at any ring size.
+static int match_batch(const Ctx &ctx)
+{
+    const int dflt = ctx.n >= (1 << 15) ? 32 : 64;
+    return std::max(1, std::min(env_int("SPFHE_MATCH_BATCH", dflt), 1024));
+}
+
+static void check_chunks(Ct *const *ch, size_t n, int level, const char *what)
+{
+    for (size_t c = 0; c < n; ++c) {
+        if (!ch[c] || !ch[c]->d) throw Error(SPFHE_EINVAL, std::string(what) + ": null chunk");
+        if (ch[c]->level != level) throw Error(SPFHE_ELEVEL, std::string(what) + ": chunk not at the top level");
+        if (std::fabs(ch[c]->scale - ch[0]->scale) > 1e-9 * std::fabs(ch[0]->scale))
+            throw Error(SPFHE_ESCALE, std::string(what) + ": chunk scales differ");
+    }
+}
+
+static size_t chunks_for(long long count, int S) { return (size_t)std::max(1LL, (count + S - 1) / S); }
+
+static const u64 *mask_montgomery(Ctx &ctx, const Pt *mask0)
+{
+    const int ell = ctx.L - 1;
+    const size_t words = (size_t)ell * ctx.n;
+    std::vector<int> mi(ell);
+    for (int i = 0; i < ell; ++i) mi[i] = i;
+    if (mask0) {
+        if (mask0->level != ell) throw Error(SPFHE_ELEVEL, "mask must be at level L-1");
+        u64 *m = ctx.rt->workspace(WS_MASK, words);
+        copy_words(ctx, m, mask0->d, words);
+        to_montgomery(ctx, m, ell, mi.data(), 1);
+        return m;
+    }
+    if (!ctx.mask0) {
+        ctx.mask0 = static_cast<u64 *>(dev_alloc(ctx, words * sizeof(u64)));
+        const double one = 1.0;
+        const double *d_one = static_cast<const double *>(ctx.rt->upload(&one, sizeof(double)));
+        encode_onehot0(ctx, d_one, 1, ell, (double)ctx.mods[ctx.L - 2], ctx.mask0);
+        to_montgomery(ctx, ctx.mask0, ell, mi.data(), 1);
+    }
+    return ctx.mask0;
+}
+
+struct Stats {
+    uint64_t matches = 0, ks_relin = 0, ks_align = 0, ks_final = 0, rescales = 0;
+};
+
+// Shared tail of both variants for one batch: rescaled products `prod`
+// ([m][2][ell][n]) are rotated to their target slots and added into their
+// result chunks.
+static void rotate_and_accumulate(Ctx &ctx, const Keys &keys, int ell, u64 *prod, int m, const std::vector<int> &rf,
+                                  const std::vector<int> &rc, Ct **C, size_t nC, Stats &st)
+{
+    Runtime &rt = *ctx.rt;
+    const long long cs = 2LL * ell * ctx.n;
+    std::vector<const u64 *> in(m);
+    for (int i = 0; i < m; ++i) in[i] = prod + i * cs;
+    u64 *W = rt.workspace(WS_MISC, (size_t)m * cs);
+    rotate_batch(ctx, keys, ell, in, rf, W, &st.ks_final);
+    for (size_t c = 0; c < nC; ++c) {
+        std::vector<int> ids;
+        for (int i = 0; i < m; ++i)
+            if (rc[i] == (int)c) ids.push_back(i);
+        if (ids.empty()) continue;
+        const int *d_ids = rt.upload_vec(ids);
+        accumulate(ctx, ell, C[c]->d, W, cs, d_ids, (int)ids.size());
+    }
+}
+
+void spmspm_ct_ct(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
+                  const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, Ct **C, size_t nC,
+                  spfhe_stats *out_stats)
+{
+    const uint64_t launches0 = ctx.launches;
+    validate_pair(A, B);
+    const int S = ctx.S, L = ctx.L;
+    const size_t n = ctx.n;
+    if (L < 3) throw Error(SPFHE_ELEVEL, "ct x ct needs L >= 3");
+    if (nA != chunks_for(A.nnz, S) || nB != chunks_for(B.nnz, S))
+        throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
+    if (nC != chunks_for((long long)A.rows * B.cols, S)) throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
+    check_chunks(Ach, nA, L, "A");
+    check_chunks(Bch, nB, L, "B");
+    if (std::fabs(Ach[0]->scale - Bch[0]->scale) > 1e-9 * Ach[0]->scale) throw Error(SPFHE_ESCALE, "A and B scales differ");
+    for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
+
+    const std::vector<MatchRec> matches = plan_alg1(A, B);
+    const double rscale = Ach[0]->scale * Bch[0]->scale / (double)ctx.mods[L - 1];
+    const int ellC = L - 2;
+    Stats st;
+    try {
+        for (size_t c = 0; c < nC; ++c) {
+            C[c] = ct_new(ctx, ellC, rscale);
+            SPFHE_CHECK_CUDA(cudaMemsetAsync(C[c]->d, 0, 2ull * ellC * n * sizeof(u64), ctx.stream));
+        }
+        if (!matches.empty()) {
+            if (!keys.relin) throw Error(SPFHE_EKEY, "no relinearisation key");
+            Runtime &rt = *ctx.rt;
+            const u64 *mask = mask_montgomery(ctx, mask0);
+            // alignment sources: (operand, chunk, amount) -> rotated-operand index
+            struct M2 {
+                int src_a, src_b;   // >= 0: rotated-operand index; < 0: -(chunk + 1) of the plain operand
+                int min_slot, rf, rc;
+            };
+            std::map<std::tuple<int, int, int>, int> rot_index;
+            std::vector<std::tuple<int, int, int>> rot_list;
+            std::vector<M2> ms(matches.size());
+            auto rot_of = [&](int op, int chunk, int amt) {
+                auto key = std::make_tuple(op, chunk, amt);
+                auto it = rot_index.find(key);
+                if (it != rot_index.end()) return it->second;
+                const int id = (int)rot_list.size();
+                rot_index[key] = id;
+                rot_list.push_back(key);
+                return id;
+            };
+            for (size_t x = 0; x < matches.size(); ++x) {
+                const MatchRec &mt = matches[x];
+                const int ca = mt.a_pos / S, sa = mt.a_pos % S, cb = mt.b_pos / S, sb = mt.b_pos % S;
+                M2 m2;
+                m2.src_a = -(ca + 1);
+                m2.src_b = -(cb + 1);
+                m2.min_slot = sa;
+                if (sa < sb) {
+                    m2.src_b = rot_of(1, cb, sb - sa);
+                } else if (sb < sa) {
+                    m2.src_a = rot_of(0, ca, sa - sb);
+                    m2.min_slot = sb;
+                }
+                const long long t = (long long)mt.i * B.cols + mt.j;
+                m2.rc = (int)(t / S);
+                m2.rf = (int)(((m2.min_slot - t % S) % S + S) % S);
+                ms[x] = m2;
+            }
+            // every key the run needs exists before the first launch
+            for (auto &r : rot_list)
+                for (int a : rotation_plan(ctx, std::get<2>(r))) rotation_key(keys, a);
+            for (auto &m2 : ms)
+                for (int a : rotation_plan(ctx, m2.rf)) rotation_key(keys, a);
+
+            const int Bm = match_batch(ctx);
+            const int G = Bm;
+            const long long csL = 2LL * L * n;
+            const int nwaves = std::max<int>(1, (int)((rot_list.size() + G - 1) / G));
+            std::vector<std::vector<int>> wave_matches(nwaves);
+            for (size_t x = 0; x < ms.size(); ++x) {
+                int w = 0;
+                if (ms[x].src_a >= 0) w = ms[x].src_a / G;
+                if (ms[x].src_b >= 0) w = ms[x].src_b / G;
+                wave_matches[w].push_back((int)x);
+            }
+            u64 *align = rt.workspace(WS_ALIGN, (size_t)std::max<size_t>(1, std::min<size_t>(G, rot_list.size())) * csL);
+            std::vector<int> mask_g_cache(S, 0);
+            for (int w = 0; w < nwaves; ++w) {
+                const int r0 = w * G, r1 = std::min<int>((int)rot_list.size(), r0 + G);
+                if (r1 > r0) {
+                    std::vector<const u64 *> rin;
+                    std::vector<int> ramt;
+                    for (int r = r0; r < r1; ++r) {
+                        const int op = std::get<0>(rot_list[r]), chunk = std::get<1>(rot_list[r]);
+                        rin.push_back((op == 0 ? Ach[chunk] : Bch[chunk])->d);
+                        ramt.push_back(std::get<2>(rot_list[r]));
+                    }
+                    rotate_batch(ctx, keys, L, rin, ramt, align, &st.ks_align);
+                }
+                auto operand = [&](int src, Ct *const *plain) -> const u64 * {
+                    if (src < 0) return plain[-src - 1]->d;
+                    return align + (long long)(src - r0) * csL;
+                };
+                const std::vector<int> &wm = wave_matches[w];
+                for (size_t b0 = 0; b0 < wm.size(); b0 += Bm) {
+                    const int m = (int)std::min<size_t>(Bm, wm.size() - b0);
+                    std::vector<const u64 *> pa(m), pb(m), d2(m), dbase(m), x1(m), x2(m), mk(m);
+                    std::vector<int> gm(m), rf(m), rc(m);
+                    u64 *D = rt.workspace(WS_TENSOR, (size_t)m * 3 * L * n);
+                    u64 *X = rt.workspace(WS_RELIN_OUT, (size_t)m * csL);
+                    u64 *Y = rt.workspace(WS_LEVEL1, (size_t)m * 2 * (L - 1) * n);
+                    u64 *Z = rt.workspace(WS_LEVEL2, (size_t)m * 2 * (L - 2) * n);
+                    u64 *T = rt.workspace(WS_RS_TMP, (size_t)m * 2 * L * n);
+                    for (int i = 0; i < m; ++i) {
+                        const M2 &m2 = ms[wm[b0 + i]];
+                        pa[i] = operand(m2.src_a, Ach);
+                        pb[i] = operand(m2.src_b, Bch);
+                        dbase[i] = D + (size_t)i * 3 * L * n;
+                        d2[i] = dbase[i] + 2 * L * n;
+                        x1[i] = X + i * csL;
+                        x2[i] = Y + (size_t)i * 2 * (L - 1) * n;
+                        mk[i] = mask;
+                        // the mask for slot p is sigma_h of the slot-0 mask, h = 5^-p
+                        gm[i] = galois_element(ctx, -m2.min_slot);
+                        rf[i] = m2.rf;
+                        rc[i] = m2.rc;
+                    }
+                    tensor(ctx, m, L, rt.upload_vec(pa), rt.upload_vec(pb), D);
+                    std::vector<KeyGroup> groups;
+                    const int gsz = 4;
+                    for (int i = 0; i < m; i += gsz) groups.push_back(KeyGroup{keys.relin, i, std::min(gsz, m - i)});
+                    keyswitch_batch(ctx, m, L, rt.upload_vec(d2), groups, rt.upload_vec(dbase), nullptr, true, X, csL);
+                    st.ks_relin += m;
+                    rescale(ctx, m, L, rt.upload_vec(x1), T, Y, 2LL * (L - 1) * n);
+                    mul_plain_perm(ctx, m, L - 1, Y, 2LL * (L - 1) * n, rt.upload_vec(mk), rt.upload_vec(gm));
+                    // Relinearize after a plaintext product has nothing to switch
+                    rescale(ctx, m, L - 1, rt.upload_vec(x2), T, Z, 2LL * (L - 2) * n);
+                    st.rescales += 2ull * m;
+                    rotate_and_accumulate(ctx, keys, L - 2, Z, m, rf, rc, C, nC, st);
+                    st.matches += m;
+                }
+            }
+        }
+        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+    } catch (...) {
+        for (size_t c = 0; c < nC; ++c)
+            if (C[c]) {
+                dev_free(ctx, C[c]->d);
+                delete C[c];
+                C[c] = nullptr;
+            }
+        throw;
+    }
+    if (out_stats) {
+        out_stats->matches = st.matches;
+        out_stats->ks_relin = st.ks_relin;
+        out_stats->ks_align = st.ks_align;
+        out_stats->ks_final = st.ks_final;
+        out_stats->rescales = st.rescales;
+        out_stats->launches = ctx.launches - launches0;
+    }
+}
+
+void spmspm_ct_pt(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
+                  const spfhe_sparse_meta &B, const double *Bvals, Pt *const *Bpts, Ct **C, size_t nC,
+                  spfhe_stats *out_stats)
+{
+    const uint64_t launches0 = ctx.launches;
+    validate_pair(A, B);
+    const int S = ctx.S, L = ctx.L;
+    const size_t n = ctx.n;
+    if (L < 2) throw Error(SPFHE_ELEVEL, "ct x pt needs L >= 2");
+    if (nA != chunks_for(A.nnz, S)) throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
+    if (nC != chunks_for((long long)A.rows * B.cols, S)) throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
+    if (!Bvals && !Bpts && B.nnz > 0) throw Error(SPFHE_EINVAL, "B values missing");
+    check_chunks(Ach, nA, L, "A");
+    for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
+    const std::vector<MatchRec> matches = plan_alg1(A, B);
+    const double wscale = (double)ctx.mods[L - 1];
+    const double rscale = Ach[0]->scale * wscale / (double)ctx.mods[L - 1];
+    const int ellC = L - 1;
+    Stats st;
+    std::vector<int> mi(L);
+    for (int i = 0; i < L; ++i) mi[i] = i;
+    try {
+        for (size_t c = 0; c < nC; ++c) {
+            C[c] = ct_new(ctx, ellC, rscale);
+            SPFHE_CHECK_CUDA(cudaMemsetAsync(C[c]->d, 0, 2ull * ellC * n * sizeof(u64), ctx.stream));
+        }
+        if (!matches.empty()) {
+            Runtime &rt = *ctx.rt;
+            std::vector<int> order(matches.size());
+            for (size_t x = 0; x < order.size(); ++x) order[x] = (int)x;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int a, int b) { return matches[a].b_pos < matches[b].b_pos; });
+            for (auto &mt : matches) {
+                const long long t = (long long)mt.i * B.cols + mt.j;
+                for (int a : rotation_plan(ctx, ((mt.a_pos % S - t % S) % S + S) % S)) rotation_key(keys, a);
+            }
+            const int Bm = match_batch(ctx);
+            const long long csL = 2LL * L * n;
+            const long long plimb = (long long)L * n;
+            for (size_t b0 = 0; b0 < order.size(); b0 += Bm) {
+                const int m = (int)std::min<size_t>(Bm, order.size() - b0);
+                // distinct B nonzeros of this batch -> weight plaintexts at slot 0
+                std::vector<int> bpos;
+                for (int i = 0; i < m; ++i) {
+                    const int bp = matches[order[b0 + i]].b_pos;
+                    if (bpos.empty() || bpos.back() != bp) bpos.push_back(bp);
+                }
+                const int np = (int)bpos.size();
+                u64 *pts = rt.workspace(WS_PTS, (size_t)np * plimb);
+                if (Bpts) {
+                    for (int p = 0; p < np; ++p) {
+                        const Pt *bp = Bpts[bpos[p]];
+                        if (!bp || bp->level != L) throw Error(SPFHE_ELEVEL, "B plaintexts must be at level L");
+                        copy_words(ctx, pts + p * plimb, bp->d, (size_t)plimb);
+                    }
+                } else {
+                    std::vector<double> vals(np);
+                    for (int p = 0; p < np; ++p) vals[p] = Bvals[bpos[p]];
+                    const double *d_vals = rt.upload_vec(vals);
+                    encode_onehot0(ctx, d_vals, np, L, wscale, pts);
+                }
+                to_montgomery(ctx, pts, L, mi.data(), np);
+                std::vector<const u64 *> src(m), ptp(m), x1(m);
+                std::vector<int> g(m), rf(m), rc(m);
+                u64 *X = rt.workspace(WS_RELIN_OUT, (size_t)m * csL);
+                u64 *Y = rt.workspace(WS_LEVEL1, (size_t)m * 2 * (L - 1) * n);
+                u64 *T = rt.workspace(WS_RS_TMP, (size_t)m * 2 * L * n);
+                int p = 0;
+                for (int i = 0; i < m; ++i) {
+                    const MatchRec &mt = matches[order[b0 + i]];
+                    while (bpos[p] != mt.b_pos) ++p;
+                    const int ca = mt.a_pos / S, sa = mt.a_pos % S;
+                    src[i] = Ach[ca]->d;
+                    ptp[i] = pts + p * plimb;
+                    x1[i] = X + i * csL;
+                    g[i] = galois_element(ctx, -sa);
+                    const long long t = (long long)mt.i * B.cols + mt.j;
+                    rc[i] = (int)(t / S);
+                    rf[i] = (int)(((sa - t % S) % S + S) % S);
+                }
+                gather_items(ctx, m, (size_t)csL, rt.upload_vec(src), X, csL);
+                mul_plain_perm(ctx, m, L, X, csL, rt.upload_vec(ptp), rt.upload_vec(g));
+                rescale(ctx, m, L, rt.upload_vec(x1), T, Y, 2LL * (L - 1) * n);
+                st.rescales += m;
+                rotate_and_accumulate(ctx, keys, L - 1, Y, m, rf, rc, C, nC, st);
+                st.matches += m;
+            }
+        }
+        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+    } catch (...) {
+        for (size_t c = 0; c < nC; ++c)
+            if (C[c]) {
+                dev_free(ctx, C[c]->d);
+                delete C[c];
+                C[c] = nullptr;
+            }
+        throw;
+    }
+    if (out_stats) {
+        out_stats->matches = st.matches;
+        out_stats->ks_relin = 0;
+        out_stats->ks_align = 0;
+        out_stats->ks_final = st.ks_final;
+        out_stats->rescales = st.rescales;
+        out_stats->launches = ctx.launches - launches0;
+    }
+}
+
+}  // namespace spfhe

@@ -1,0 +1,64 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point include/spfhe.h declares, and its host-only planner (Alg. 1) matches
+the oracle's merge exactly and rejects malformed metadata."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import spmspm
+from paper_2604_11659_gb300 import synthetic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_2604_11659_gb300 import build, spfhe
+    build.build()
+    spfhe.lib()
+    return spfhe
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "spfhe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spfhe_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(sp):
+    names = _declared()
+    assert len(names) >= 30
+    lib = sp.lib()
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert sorted(sp.EXPORTED) == names
+
+
+@pytest.mark.parametrize("seed,rows,inner,cols,s", [(0, 6, 5, 4, 0.5), (1, 16, 16, 16, 0.75), (2, 9, 3, 7, 0.9),
+                                                    (3, 5, 5, 5, 1.0), (4, 128, 128, 128, 0.9)])
+def test_planner_matches_oracle(sp, seed, rows, inner, cols, s):
+    rng = np.random.default_rng(seed)
+    A = synthetic.bernoulli_sparse(rng, rows, inner, s)
+    B = synthetic.bernoulli_sparse(rng, inner, cols, s)
+    Aip, Aix, _ = spmspm.dense_to_csr(A)
+    Bip, Bix, _ = spmspm.dense_to_csc(B)
+    got = sp.spfhe_plan_matches(sp.sparse_meta(Aip, Aix, rows, inner), sp.sparse_meta(Bip, Bix, inner, cols))
+    want = [(m.i, m.j, m.k, m.a_pos, m.b_pos) for m in spmspm.alg1_matches(Aip, Aix, Bip, Bix, rows, cols)]
+    assert [tuple(int(v) for v in r) for r in got] == want
+
+
+def test_planner_rejects_malformed_metadata(sp):
+    ip = np.array([0, 2, 3], np.int32)
+    ix = np.array([0, 1, 1], np.int32)
+    good = sp.sparse_meta(ip, ix, 2, 2)
+    bad_range = sp.sparse_meta(ip, np.array([0, 5, 1], np.int32), 2, 2)
+    unsorted = sp.sparse_meta(ip, np.array([1, 0, 1], np.int32), 2, 2)
+    non_mono = sp.sparse_meta(np.array([0, 3, 2], np.int32), ix, 2, 2)
+    for bad in (bad_range, unsorted, non_mono):
+        with pytest.raises(sp.SpfheError) as e:
+            sp.spfhe_plan_matches(bad, good)
+        assert e.value.status == -1
+    with pytest.raises(sp.SpfheError):
+        sp.spfhe_plan_matches(good, sp.sparse_meta(ip, ix, 3, 2))   # inner dims differ

@@ -18,6 +18,7 @@
  * multiplication primitive (itself pinned against the O(n^2) definitions
  * or_ntt_direct and or_negacyclic_schoolbook by the tests).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -267,6 +268,61 @@ void or_bconv(const u64 *x, const u64 *src, int ns, u64 *out, const u64 *dst, in
     free(hat_mod);
 }
 
+/* Conversion of x (limbs over the moduli src[0..ns)) to its CENTRED
+ * representative [x]_D in [-D/2, D/2), D = prod src, reduced mod dst[t]:
+ *   y_i = [x_i * (D/src_i)^{-1}]_{src_i},
+ *   v   = round(f),  f = fma(y_i, 1/src_i, f) over i ascending from f = 0
+ *         (IEEE double; 1/src_i the correctly rounded reciprocal),
+ *   out_t = sum_i y_i * (D/src_i) - v * D   mod dst_t.
+ * sum_i y_i (D/src_i) equals x mod D plus u*D with u = floor(sum_i y_i/src_i);
+ * subtracting round(.) instead removes that overflow and centres the result
+ * (the floating-point correction of Halevi, Polyakov and Shoup, "An Improved
+ * RNS Variant of the BFV Homomorphic Encryption Scheme", CT-RSA 2019).  A
+ * fractional part within ~2^-50 of one half may round the other way, giving
+ * the other representative; the value is then off by D on that coefficient. */
+void or_bconv_centred(const u64 *x, const u64 *src, int ns, u64 *out, const u64 *dst, int nd, int n)
+{
+    u64 *hat_inv = (u64 *)malloc(sizeof(u64) * ns);
+    u64 *hat_mod = (u64 *)malloc(sizeof(u64) * ns * nd);
+    u64 *D_mod = (u64 *)malloc(sizeof(u64) * nd);
+    for (int i = 0; i < ns; i++) {
+        u64 h = 1;
+        for (int k = 0; k < ns; k++) if (k != i) h = mulmod(h, src[k] % src[i], src[i]);
+        hat_inv[i] = or_invmod(h, src[i]);
+        for (int t = 0; t < nd; t++) {
+            u64 ht = 1 % dst[t];
+            for (int k = 0; k < ns; k++) if (k != i) ht = mulmod(ht, src[k] % dst[t], dst[t]);
+            hat_mod[i * nd + t] = ht;
+        }
+    }
+    for (int t = 0; t < nd; t++) {
+        u64 d = 1 % dst[t];
+        for (int k = 0; k < ns; k++) d = mulmod(d, src[k] % dst[t], dst[t]);
+        D_mod[t] = d;
+    }
+    u64 *y = (u64 *)malloc(sizeof(u64) * ns);
+    double *inv = (double *)malloc(sizeof(double) * ns);
+    for (int i = 0; i < ns; i++) inv[i] = 1.0 / (double)src[i];
+    for (int c = 0; c < n; c++) {
+        double f = 0.0;
+        for (int i = 0; i < ns; i++) {
+            y[i] = mulmod(x[(size_t)i * n + c], hat_inv[i], src[i]);
+            f = fma((double)y[i], inv[i], f);
+        }
+        u64 v = (u64)nearbyint(f);
+        for (int t = 0; t < nd; t++) {
+            u64 acc = 0;
+            for (int i = 0; i < ns; i++) acc = addmod(acc, mulmod(y[i], hat_mod[i * nd + t], dst[t]), dst[t]);
+            out[(size_t)t * n + c] = submod(acc, mulmod(v, D_mod[t], dst[t]), dst[t]);
+        }
+    }
+    free(y);
+    free(inv);
+    free(D_mod);
+    free(hat_inv);
+    free(hat_mod);
+}
+
 /* ------------------------------------------------------------------ */
 /* CKKS over a fixed parameter set                                     */
 /* ------------------------------------------------------------------ */
@@ -286,10 +342,13 @@ static int ext_mod_index(const or_params *P, int ell, int t) { return t < ell ? 
  * key ksk = {(k0_j, k1_j)}_j stored as [dnum][2][L+K][n] (coefficient
  * domain, limbs over the full basis q_0..q_{L-1}, p_0..p_{K-1}).
  *   digits: consecutive groups of alpha = ceil(L/dnum) limbs of Q_ell
- *   ModUp:  digit j -> Q_ell u P by fast basis conversion (limbs of the digit
- *           itself are kept as they are)
+ *   ModUp:  digit j -> Q_ell u P: the centred representative of the digit
+ *           value modulo its modulus Q_j (or_bconv_centred) is converted to
+ *           every other modulus; the digit's own limbs are kept as they are
  *   IP:     acc_b = sum_j ext_j * k_b,j  (ring products, limb by limb)
- *   ModDown: out_b = (acc_b|Q - Conv_{P->Q}(acc_b|P)) * P^{-1}  mod q_i
+ *   ModDown: out_b = (acc_b|Q - [acc_b]_P) * P^{-1}  mod q_i with [.]_P the
+ *            centred representative (or_bconv_centred), i.e. out_b is
+ *            acc_b / P rounded to the nearest integer, coefficient-wise
  * out0, out1: ell limbs each. */
 void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64 *out0, u64 *out1)
 {
@@ -313,7 +372,7 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
             if (t >= lo && t < hi) {
                 memcpy(ext + t * ln, c + t * ln, sizeof(u64) * ln);
             } else {
-                or_bconv(c + lo * ln, P->mods + lo, hi - lo, ext + t * ln, &ext_mods[t], 1, n);
+                or_bconv_centred(c + lo * ln, P->mods + lo, hi - lo, ext + t * ln, &ext_mods[t], 1, n);
             }
         }
         /* inner product with the key */
@@ -336,7 +395,7 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
     }
     u64 *conv = (u64 *)malloc(sizeof(u64) * ell * ln);
     for (int b = 0; b < 2; b++) {
-        or_bconv(acc[b] + (size_t)ell * ln, P->mods + L, K, conv, P->mods, ell, n);
+        or_bconv_centred(acc[b] + (size_t)ell * ln, P->mods + L, K, conv, P->mods, ell, n);
         u64 *out = b == 0 ? out0 : out1;
         for (int i = 0; i < ell; i++)
             for (int k = 0; k < n; k++)

@@ -97,3 +97,61 @@ def test_automorphism_monomials_and_homomorphism():
     assert np.array_equal(ckks.automorphism(ckks.automorphism(a, g, q), h, q),
                           ckks.automorphism(a, (g * h) % (2 * n), q))
     assert np.array_equal(ckks.automorphism(a, 1, q), a)
+
+
+def test_centred_bconv_is_the_centred_representative():
+    """or_bconv_centred returns [x]_D in [-D/2, D/2) reduced mod each target
+    (checked with Python integers)."""
+    import ctypes
+    n = 64
+    src = ckks.gen_primes(5, 60, 4)
+    dst = ckks.gen_primes(5, 45, 3)
+    rng = np.random.default_rng(11)
+    x = np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in src])
+    D = 1
+    for q in src:
+        D *= q
+    # include values at the two ends of the centred range
+    for c, X in ((0, D // 2 - 1), (1, D // 2), (2, D - 1), (3, 0)):
+        for i, q in enumerate(src):
+            x[i, c] = X % q
+    out = np.zeros((len(dst), n), np.uint64)
+    L = ckks.lib()
+    L.or_bconv_centred.argtypes = [ckks.u64p, ckks.u64p, ctypes.c_int, ckks.u64p, ckks.u64p, ctypes.c_int, ctypes.c_int]
+    s = np.array(src, np.uint64)
+    d = np.array(dst, np.uint64)
+    L.or_bconv_centred(ckks._p(x), ckks._p(s), len(src), ckks._p(out), ckks._p(d), len(dst), n)
+    for c in range(n):
+        X, _ = _crt([x[i, c] for i in range(len(src))], src)
+        cen = X if X < D // 2 else X - D
+        if c in (0, 1):
+            # X/D within 2^-200 of one half: either representative is valid
+            assert all(int(out[t, c]) in (cen % p, (cen + D) % p, (cen - D) % p) for t, p in enumerate(dst))
+            continue
+        assert [int(out[t, c]) for t in range(len(dst))] == [cen % p for p in dst]
+
+
+def test_moddown_rounds_to_nearest():
+    """Key switching output decrypts to c*s' + e with e zero-mean: the mean of
+    the error over all coefficients is far below the floor+overflow bias
+    (about (K-1)/2 * sum(s)) that an uncorrected conversion leaves."""
+    from tests.oracle_util import oracle_params
+    from paper_2604_11659_gb300 import synthetic
+    P = oracle_params(synthetic.ring_tiny(log_n=10, L=4, dnum=1))
+    o = ckks.Oracle(P)
+    keys = o.keygen(2)
+    rng = np.random.default_rng(4)
+    s_rns = o.small_to_rns(keys.s)
+    s2 = o.rns_polymul(s_rns, s_rns, np.arange(P.L + P.K, dtype=np.int32))
+    errs = []
+    for _ in range(4):
+        c = np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in P.q])
+        k0, k1 = o.keyswitch(c, keys.relin)
+        mi = np.arange(P.L, dtype=np.int32)
+        got = (k0[0] + o.rns_polymul(k1, s_rns[: P.L], mi)[0]) % np.uint64(P.q[0])
+        want = o.rns_polymul(c, s2[: P.L], mi)[0]
+        q0 = P.q[0]
+        errs.extend(((int(a) - int(b) + q0 // 2) % q0) - q0 // 2 for a, b in zip(got, want))
+    errs = np.array(errs, dtype=np.float64)
+    # zero-mean rounding: |mean| well inside a few standard errors
+    assert abs(errs.mean()) < 5 * errs.std() / np.sqrt(errs.size)

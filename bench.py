@@ -1,0 +1,452 @@
+"""Benchmark: encrypted 128x128 sparse x sparse matmuls per second (CKKS,
+N = 2^16, L = 24, dnum = 3), Alg. 1 + Alg. 2 through libspfhe.
+
+One step = one complete encrypted product C = A B (every match of Alg. 1:
+alignment rotations, tensor, relinearisation, two rescales, mask, final
+rotation, accumulation) on ciphertexts already resident in HBM.  The working
+set (switching keys ~37 GB, batch buffers ~10 GB) is far larger than the
+129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); keyswitch HBM GB/s; p99"
+ALU_CLASSES = {"ntt_fwd", "ntt_inv", "modup_bconv", "moddown_bconv"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def alu_peak_mulmods(sm_mhz: float) -> float:
+    """64-bit modular multiplies per second the INT32 multipliers allow:
+    152 SMs x 64 IMAD lanes per clock x clock / 10 32-bit partial products per
+    64-bit Shoup or Montgomery modmul (4 for the high 64 bits of a 64x64
+    product, 3 + 3 for the two low-half products)."""
+    return 152 * 64 * sm_mhz * 1e6 / 10.0
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(name: str, seed: int):
+    from paper_2604_11659_gb300 import synthetic
+    if name == "128x128":
+        return synthetic.case_128x128(seed=seed)
+    if name == "16x16":
+        return synthetic.case_16x16(seed=seed)
+    raise SystemExit("unknown workload " + name)
+
+
+def to_csr(M):
+    ip, ix, d = [0], [], []
+    for row in M:
+        nz = np.nonzero(row)[0]
+        ix.extend(nz.tolist())
+        d.extend(row[nz].tolist())
+        ip.append(len(ix))
+    return np.array(ip, np.int32), np.array(ix, np.int32), np.array(d, np.float64)
+
+
+class GpuMatmul:
+    """Keys, encrypted operands and the matmul call for one workload."""
+
+    def __init__(self, case, rot_base, stream):
+        from paper_2604_11659_gb300 import params as gparams
+        from paper_2604_11659_gb300 import spfhe
+        self.sp = spfhe
+        rec = case.ring
+        self.rec = rec
+        self.case = case
+        self.gp = gparams.ctx_params(rec, rot_base=rot_base)
+        self.K = self.gp.K
+        self.ctx = spfhe.spfhe_ctx_create(self.gp, stream)
+        self.n = 1 << rec.log_n
+        self.S = self.n // 2
+        t = time.time()
+        self.keys = spfhe.spfhe_keygen(self.ctx, 20260101)
+        self.keygen_s = time.time() - t
+        A, B = case.A, case.B
+        self.rows, self.inner, self.cols = A.shape[0], A.shape[1], B.shape[1]
+        Aip, Aix, Ad = to_csr(A)
+        Bip, Bix, Bd = to_csr(B.T)
+        self.Am = spfhe.sparse_meta(Aip, Aix, self.rows, self.inner)
+        self.Bm = spfhe.sparse_meta(Bip, Bix, self.inner, self.cols)
+        self.nnz = (len(Ad), len(Bd))
+        self.A_cts = self._encrypt_chunks(Ad, 1)
+        self.B_cts = self._encrypt_chunks(Bd, 1000)
+        self.n_c = max(1, -(-(self.rows * self.cols) // self.S))
+        spfhe.spfhe_sync(self.ctx)
+
+    def _encrypt_chunks(self, data, seed0):
+        sp = self.sp
+        out = []
+        nch = max(1, -(-len(data) // self.S))
+        for c in range(nch):
+            z = np.zeros(self.S)
+            part = data[c * self.S:(c + 1) * self.S]
+            z[: len(part)] = part
+            pt = sp.spfhe_encode(self.ctx, z, self.rec.L, self.rec.scale)
+            out.append(sp.spfhe_encrypt(self.ctx, self.keys, pt, seed0 + c))
+            sp.spfhe_pt_free(pt)
+        return out
+
+    def step(self, A_cts=None, B_cts=None):
+        outs, stats = self.sp.spfhe_sparse_matmul_ct_ct(self.ctx, self.keys, self.Am, A_cts or self.A_cts, self.Bm,
+                                                        B_cts or self.B_cts, None, self.n_c)
+        return outs, stats
+
+    def free(self, outs):
+        for h in outs:
+            self.sp.spfhe_ct_free(h)
+
+    def check(self, outs):
+        """Decrypted result vs the FP64 product (max abs error)."""
+        sp = self.sp
+        vals = []
+        for h in outs:
+            pt = sp.spfhe_decrypt(self.ctx, self.keys, h)
+            vals.append(sp.spfhe_decode(self.ctx, pt, self.S).real)
+            sp.spfhe_pt_free(pt)
+        C = np.concatenate(vals)[: self.rows * self.cols].reshape(self.rows, self.cols)
+        return float(np.max(np.abs(C - self.case.A @ self.case.B)))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Times the plain CPU oracle on one sample of the workload's per-match
+    operations at the workload's ring parameters and projects matmuls/s with
+    the workload's exact op counts (from the oracle's own Alg. 1 planner)."""
+
+    def __init__(self, case, rot_base):
+        from oracle import build as obuild
+        obuild.build()
+        from oracle import ckks, spmspm
+        self.ck, self.sm = ckks, spmspm
+        rec = case.ring
+        K = ckks.special_prime_count(rec.q_bits, rec.dnum, rec.p_bits, rec.k_stated)
+        self.P = ckks.make_params(rec.log_n, rec.q_bits, K, rec.dnum, rec.scale, rot_base=rot_base)
+        self.o = ckks.Oracle(self.P)
+        self.keys = self.o.keygen(7)   # relinearisation key only
+        P = self.P
+        rng = np.random.default_rng(3)
+        self.a = self.o.encrypt(self.o.encode(rng.uniform(-1, 1, P.slots), P.L, P.scale), self.keys, rng)
+        self.b = self.o.encrypt(self.o.encode(rng.uniform(-1, 1, P.slots), P.L, P.scale), self.keys, rng)
+        # exact op counts of the workload
+        Aip, Aix, _ = spmspm.dense_to_csr(case.A)
+        Bip, Bix, _ = spmspm.dense_to_csc(case.B)
+        S = P.slots
+        ms = spmspm.alg1_matches(Aip, Aix, Bip, Bix, case.A.shape[0], case.B.shape[1])
+        cols = case.B.shape[1]
+        self.matches = len(ms)
+        self.ks_final = sum(len(ckks.rotation_plan((min(m.a_pos % S, m.b_pos % S) - (m.i * cols + m.j) % S) % S, S,
+                                                   rot_base)) for m in ms)
+        deltas = {("B" if m.a_pos % S < m.b_pos % S else "A", m.a_pos // S if m.a_pos % S > m.b_pos % S else m.b_pos // S,
+                   abs(m.a_pos % S - m.b_pos % S)) for m in ms if m.a_pos % S != m.b_pos % S}
+        self.ks_align = sum(len(ckks.rotation_plan(d, S, rot_base)) for _, _, d in deltas)
+
+    def run(self):
+        """One timed sample; returns (seconds of CPU work, projected seconds per matmul)."""
+        o, P = self.o, self.P
+        t0 = time.perf_counter()
+        d0, d1, d2, sc = o.tensor(self.a, self.b)
+        t1 = time.perf_counter()
+        ct = o.relinearize(d0, d1, d2, sc, self.keys)
+        t2 = time.perf_counter()
+        ct = o.rescale(ct)
+        t3 = time.perf_counter()
+        ct = o.mul_plain(ct, o.encode_onehot(1.0, 3, ct.level, float(P.q[ct.level - 1])))
+        t4 = time.perf_counter()
+        ct = o.rescale(ct)
+        t5 = time.perf_counter()
+        o.keyswitch(ct.c1, self.keys.relin)   # one key switch at level L-2 (a final-rotation step)
+        t6 = time.perf_counter()
+        o.add(ct, ct)
+        t7 = time.perf_counter()
+        t_tensor, t_ks_top, t_rs1 = t1 - t0, t2 - t1, t3 - t2
+        t_mask, t_rs2, t_ks_low, t_add = t4 - t3, t5 - t4, t6 - t5, t7 - t6
+        per_match = t_tensor + t_ks_top + t_rs1 + t_mask + t_rs2 + t_add
+        projected = self.matches * per_match + self.ks_final * t_ks_low + self.ks_align * t_ks_top
+        return t7 - t0, projected
+
+
+def cpu_baseline_line(case, rot_base):
+    s = OracleSample(case, rot_base)
+    cpu_s, proj = s.run()
+    return {"value": 1.0 / proj, "unit": "matmuls/s", "cores": 1, "kind": "oracle",
+            "sample": ("one tensor + relinearisation + 2 rescales + mask product + key switch at level L-2 + add "
+                       "at N=2^16, L=24, dnum=3 (%.1f s of CPU work), projected with the workload's exact counts: "
+                       "%d matches, %d final-rotation and %d alignment key switches"
+                       % (cpu_s, s.matches, s.ks_final, s.ks_align))}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    case = make_workload(args.workload, args.seed)
+    s = OracleSample(case, args.rot_base)
+    for _ in range(args.warmup):
+        s.run()
+    times = []
+    cpu_total = 0.0
+    for _ in range(args.steps):
+        cpu_s, proj = s.run()
+        cpu_total += cpu_s
+        times.append(proj)
+    per = statistics.mean(times)
+    val = 1.0 / per
+    line = {"metric": METRIC, "value": val, "unit": "matmuls/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "128x128 ct x ct, 90% sparsity, N=2^16, L=24, dnum=3, K=7, rot_base=%d"
+                       % args.rot_base, "l2": "working set >> L2"},
+            "cpu_baseline": {"value": val, "unit": "matmuls/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: one sample of the per-match ops (%.1f s CPU), projected with "
+                                       "exact op counts (%d matches)" % (cpu_total / args.steps, s.matches)},
+            "e2e": {"value": val, "unit": "matmuls/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spfhe", choices=["spfhe", "reference"])
+    ap.add_argument("--workload", default="128x128", choices=["128x128", "16x16"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--rot-base", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.workload == "16x16" and args.rot_base == 256:
+        args.rot_base = 16
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2604_11659_gb300 import build as gbuild
+    gbuild.build()
+    stream = torch.cuda.current_stream().cuda_stream
+    case = make_workload(args.workload, args.seed + rank)
+    g = GpuMatmul(case, args.rot_base, stream)
+    sp = g.sp
+
+    for _ in range(max(3, args.warmup)):
+        outs, st = g.step()
+        g.free(outs)
+    torch.cuda.synchronize()
+
+    # timed region: device events on the context stream, per-kernel profile live
+    sp.spfhe_prof_enable(g.ctx, True)
+    launches0 = sp.spfhe_launch_count(g.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        last = None
+        for k in range(args.steps):
+            outs, st = g.step()
+            if k < args.steps - 1:
+                g.free(outs)
+            else:
+                last = outs
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = sp.spfhe_launch_count(g.ctx) - launches0
+    prof = sp.spfhe_prof_all(g.ctx)
+    ks_info = sp.spfhe_prof_keyswitch(g.ctx)
+    sp.spfhe_prof_enable(g.ctx, False)
+    err = g.check(last)
+    g.free(last)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    Lr = g.rec.L
+    A_host = [sp.spfhe_ct_export(g.ctx, h, g.n, out=_pinned((2, Lr, g.n))) for h in g.A_cts]
+    B_host = [sp.spfhe_ct_export(g.ctx, h, g.n, out=_pinned((2, Lr, g.n))) for h in g.B_cts]
+    C_host = [_pinned((2, Lr - 2, g.n)) for _ in range(g.n_c)]
+    h2d = sum(a.nbytes for a in A_host + B_host)
+    d2h = sum(c.nbytes for c in C_host)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ga = [sp.spfhe_ct_import(g.ctx, a.ctypes.data, Lr, g.rec.scale) for a in A_host]
+        gb = [sp.spfhe_ct_import(g.ctx, b.ctypes.data, Lr, g.rec.scale) for b in B_host]
+        outs, _ = g.step(ga, gb)
+        for h, buf in zip(outs, C_host):
+            sp.spfhe_ct_export(g.ctx, h, g.n, out=buf)
+        g.free(outs + ga + gb)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world / e2e_s
+
+    hbm_peak, sm_max, peak_src = load_peaks()
+    kernels = {}
+    for name, d in prof.items():
+        if d["launches"]:
+            kernels[name] = {"launches": d["launches"], "ms": round(d["ms"], 3),
+                             "share": round(d["ms"] / max(1e-9, sum(v["ms"] for v in prof.values())), 4),
+                             "gbs": round(d["bytes"] / max(1e-12, d["ms"] * 1e-3) / 1e9, 1)}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dd = prof[dom]
+    if dom in ALU_CLASSES:
+        peak = alu_peak_mulmods(sm_max)
+        achieved = dd["work"] / (dd["ms"] * 1e-3)
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "Tmulmod/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
+                "bytes_per_launch": dd["bytes"] / max(1, dd["launches"])}
+    else:
+        achieved = dd["bytes"] / (dd["ms"] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src}
+    ks_cls = ["modup_bconv", "ks_inner_product", "moddown_bconv", "moddown_final", "ks_ntt_fwd", "ks_ntt_inv"]
+    ks_ms = sum(prof[c]["ms"] for c in ks_cls)
+    ks_calls, ks_bytes = ks_info
+
+    line = {"metric": METRIC, "value": value, "unit": "matmuls/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "%s ct x ct, %d%% sparsity, N=2^%d, L=%d, dnum=%d, K=%d, rot_base=%d"
+                       % (args.workload, round(100 * (1 - g.nnz[0] / (g.rows * g.inner))), g.rec.log_n, Lr,
+                          g.rec.dnum, g.K, args.rot_base),
+                       "matches": st["matches"], "ks_per_step": st["ks_relin"] + st["ks_align"] + st["ks_final"],
+                       "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},
+            "e2e": {"value": e2e_val, "unit": "matmuls/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+            "max_abs_err": err, "keygen_s": round(g.keygen_s, 2),
+            "keyswitch": {"polys": ks_calls, "gbs": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9,
+                          "frac_of_hbm": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9 / hbm_peak},
+            "kernels": kernels}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(case, args.rot_base)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+_PINNED = []
+
+
+def _pinned(shape):
+    import torch
+    t = torch.empty(shape, dtype=torch.int64).pin_memory()
+    _PINNED.append(t)
+    return t.numpy().view(np.uint64)
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,11 @@ spfhe_status spfhe_prof_enable(spfhe_ctx *ctx, int enable);
 spfhe_status spfhe_prof_read(spfhe_ctx *ctx, int cls, uint64_t *launches, double *ms, double *bytes, double *work);
 int spfhe_prof_classes(void);
 const char *spfhe_prof_class_name(int cls);
+/* Key switching as a whole since the last spfhe_prof_enable: number of
+ * key-switched polynomials and their algorithmic bytes (input polynomial,
+ * output pair, and the switching key once per group of polynomials that
+ * share it in one launch). */
+spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes);
 
 /* ---- keys ------------------------------------------------------------ */
 /* Sample a ternary secret, the relinearisation key and one rotation key per

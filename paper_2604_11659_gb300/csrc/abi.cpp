@@ -180,6 +180,15 @@ spfhe_status spfhe_prof_read(spfhe_ctx *ctx, int cls, uint64_t *launches, double
 
 int spfhe_prof_classes(void) { return K_NCLASS; }
 
+spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes)
+{
+    return guard([&] {
+        Ctx &c = C(ctx);
+        if (calls) *calls = c.prof.ks_calls;
+        if (bytes) *bytes = c.prof.ks_bytes;
+    });
+}
+
 const char *spfhe_prof_class_name(int cls) { return kernel_class_name(cls); }
 
 spfhe_status spfhe_keygen(spfhe_ctx *ctx, uint64_t seed, spfhe_keys **out)

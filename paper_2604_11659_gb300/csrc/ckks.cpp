@@ -24,6 +24,13 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
     u64 *ext = rt.workspace(WS_KS_EXT, (size_t)items * ext_stride);
     u64 *acc = rt.workspace(WS_KS_ACC, (size_t)items * acc_stride);
     u64 *conv = rt.workspace(WS_KS_CONV, (size_t)items * 2 * ell * n);
+    struct InKs {
+        Ctx &c;
+        explicit InKs(Ctx &x) : c(x) { ++c.in_keyswitch; }
+        ~InKs() { --c.in_keyswitch; }
+    } in_ks(ctx);
+    ctx.prof.ks_calls += items;
+    ctx.prof.ks_bytes += 8.0 * n * (3.0 * ell * items + 2.0 * beta * next * groups.size());
     // ModUp: coefficient representation of every input limb, then one base
     // conversion per digit and forward transforms of the new limbs
     gather_items(ctx, items, (size_t)coef_stride, d_in, coef, coef_stride);

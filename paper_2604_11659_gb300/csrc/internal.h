@@ -47,9 +47,13 @@ struct DevTables {
     // hat_inv[(hi-1)*alpha + i] (Shoup pair) and for every target modulus t
     // hat_mont[((hi-1)*alpha + i) * M + t] = (D/q_i mod m_t) * 2^64 mod m_t.
     u64 *mu_hat_inv = nullptr, *mu_hat_inv_p = nullptr, *mu_hat_mont = nullptr;
+    // digit modulus D = prod_{i in [lo, hi)} q_i modulo every target: [(hi-1) * M + t] (Shoup pair)
+    u64 *mu_dmod = nullptr, *mu_dmod_p = nullptr;
+    double *inv_q = nullptr;                       // [M] 1 / m (correctly rounded double)
     // ModDown P -> Q: hat_inv over p_k, hat_mont[k * M + i], and P^{-1} mod q_i.
     u64 *md_hat_inv = nullptr, *md_hat_inv_p = nullptr, *md_hat_mont = nullptr;
     u64 *md_pinv = nullptr, *md_pinv_p = nullptr;   // [L]
+    u64 *md_pmod = nullptr, *md_pmod_p = nullptr;   // [L] P mod q_i (Shoup pair)
     // Rescale dropping q_t: rs_inv[t * L + i] = q_t^{-1} mod q_i (Shoup pair),
     // rs_qt[t * L + i] = q_t mod q_i.
     u64 *rs_inv = nullptr, *rs_inv_p = nullptr, *rs_qt = nullptr;
@@ -58,7 +62,7 @@ struct DevTables {
 // Kernel classes for launch accounting and the profiler.
 enum KClass {
     K_NTT_FWD = 0, K_NTT_INV, K_MODUP, K_IP, K_MODDOWN_BCONV, K_MODDOWN_FINAL, K_TENSOR, K_RESCALE,
-    K_AUTOMORPH, K_MASK, K_ACCUM, K_OTHER, K_NCLASS
+    K_AUTOMORPH, K_MASK, K_ACCUM, K_OTHER, K_KS_NTT_FWD, K_KS_NTT_INV, K_NCLASS
 };
 
 struct ProfRec {
@@ -74,6 +78,10 @@ struct Prof {
     uint64_t launches[K_NCLASS] = {};
     uint64_t timed[K_NCLASS] = {};
     double bytes[K_NCLASS] = {}, work[K_NCLASS] = {}, ms[K_NCLASS] = {};
+    // key switching as a whole: calls and algorithmic bytes (input poly,
+    // output pair, and each key stream once per item group sharing it)
+    uint64_t ks_calls = 0;
+    double ks_bytes = 0;
 };
 
 struct Ctx {
@@ -92,6 +100,7 @@ struct Ctx {
     struct Runtime *rt = nullptr;    // workspace cache + metadata ring
     double *cos_tab = nullptr;       // cos(pi j / n), j < n (device), for one-hot encodings
     Prof prof;
+    int in_keyswitch = 0;            // NTT launches inside key switching are classed separately
 };
 
 struct Keys {

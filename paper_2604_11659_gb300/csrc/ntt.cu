@@ -246,12 +246,12 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
+        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
+        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
     }
 }
 
@@ -265,12 +265,12 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
+        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
+        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
     }
 }
 

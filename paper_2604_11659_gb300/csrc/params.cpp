@@ -186,12 +186,28 @@ void upload_tables(Ctx &ctx)
             }
         }
     }
+    std::vector<u64> dmod((size_t)L * M), dmodp((size_t)L * M);
+    for (int hi = 1; hi <= L; ++hi) {
+        const int lo = ((hi - 1) / A) * A;
+        for (int tt = 0; tt < M; ++tt) {
+            const u64 m = ctx.mods[tt];
+            u64 d = 1 % m;
+            for (int k = lo; k < hi; ++k) d = mulmod_host(d, ctx.mods[k] % m, m);
+            dmod[(size_t)(hi - 1) * M + tt] = d;
+            dmodp[(size_t)(hi - 1) * M + tt] = shoup_pre(d, m);
+        }
+    }
+    t.mu_dmod = upload(dmod);
+    t.mu_dmod_p = upload(dmodp);
+    std::vector<double> invq(M);
+    for (int i = 0; i < M; ++i) invq[i] = 1.0 / (double)ctx.mods[i];
+    t.inv_q = upload(invq);
     t.mu_hat_inv = upload(hinv);
     t.mu_hat_inv_p = upload(hinvp);
     t.mu_hat_mont = upload(hmont);
 
     // ModDown P -> Q
-    std::vector<u64> dinv(K), dinvp(K), dmont((size_t)K * M), pinv(L), pinvp(L);
+    std::vector<u64> dinv(K), dinvp(K), dmont((size_t)K * M), pinv(L), pinvp(L), pmod(L), pmodp(L);
     for (int k = 0; k < K; ++k) {
         const u64 pk = ctx.mods[L + k];
         u64 d = 1;
@@ -213,12 +229,16 @@ void upload_tables(Ctx &ctx)
         for (int k = 0; k < K; ++k) P = mulmod_host(P, ctx.mods[L + k] % qi, qi);
         pinv[i] = invmod_host(P, qi);
         pinvp[i] = shoup_pre(pinv[i], qi);
+        pmod[i] = P;
+        pmodp[i] = shoup_pre(P, qi);
     }
     t.md_hat_inv = upload(dinv);
     t.md_hat_inv_p = upload(dinvp);
     t.md_hat_mont = upload(dmont);
     t.md_pinv = upload(pinv);
     t.md_pinv_p = upload(pinvp);
+    t.md_pmod = upload(pmod);
+    t.md_pmod_p = upload(pmodp);
 
     // Rescale
     std::vector<u64> rinv((size_t)L * L, 0), rinvp((size_t)L * L, 0), rqt((size_t)L * L, 0);
@@ -239,10 +259,12 @@ void free_tables(Ctx &ctx)
     DevTables &t = ctx.dt;
     u64 *ptrs[] = {t.tw, t.twp, t.itw, t.itwp, t.mu_hat_inv, t.mu_hat_inv_p, t.mu_hat_mont,
                    t.md_hat_inv, t.md_hat_inv_p, t.md_hat_mont, t.md_pinv, t.md_pinv_p,
+                   t.md_pmod, t.md_pmod_p, t.mu_dmod, t.mu_dmod_p,
                    t.rs_inv, t.rs_inv_p, t.rs_qt};
     for (u64 *p : ptrs)
         if (p) cudaFree(p);
     if (t.mc) cudaFree(t.mc);
+    if (t.inv_q) cudaFree(t.inv_q);
     t = DevTables{};
 }
 

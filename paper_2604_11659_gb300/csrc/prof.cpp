@@ -9,7 +9,8 @@ const char *kernel_class_name(int cls)
 {
     static const char *names[K_NCLASS] = {"ntt_fwd", "ntt_inv", "modup_bconv", "ks_inner_product",
                                           "moddown_bconv", "moddown_final", "tensor", "rescale",
-                                          "automorph", "mask_mul", "accumulate", "other"};
+                                          "automorph", "mask_mul", "accumulate", "other", "ks_ntt_fwd",
+                                          "ks_ntt_inv"};
     return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
 }
 
@@ -50,9 +51,12 @@ void prof_reset(Ctx &ctx, bool on)
     p.on = on;
     p.used = 0;
     p.recs.clear();
+    p.ks_calls = 0;
+    p.ks_bytes = 0;
     for (int c = 0; c < K_NCLASS; ++c) {
         p.launches[c] = 0;
         p.bytes[c] = p.work[c] = p.ms[c] = 0;
+        p.timed[c] = 0;
     }
 }
 

@@ -53,13 +53,16 @@ __global__ void k_automorph(int polys, int ell, int log_n, const u64 *const *in,
 }
 
 // ModUp: for digit j (blockIdx.y) with source limbs [lo, hi) of the
-// coefficient-domain input, write the converted value into every extended
-// limb t outside [lo, hi).  Extended limb t < ell is q_t, t >= ell is
-// p_{t-ell} (global modulus L + t - ell).
+// coefficient-domain input, write the centred representative of the digit
+// value modulo D = prod q_i into every extended limb t outside [lo, hi):
+//   y_i = [x_i (D/q_i)^{-1}]_{q_i},  v = round(sum_i y_i / q_i) (fma chain),
+//   out_t = sum_i y_i (D/q_i) - v D  mod m_t.
+// Extended limb t < ell is q_t, t >= ell is p_{t-ell} (modulus L + t - ell).
 __global__ void k_modup_bconv(int ell, int L, int K, int alpha, int M, int n, const u64 *coef, long long coef_stride,
                               u64 *ext, long long ext_stride, const ModConst *__restrict__ mc,
                               const u64 *__restrict__ hinv, const u64 *__restrict__ hinvp,
-                              const u64 *__restrict__ hmont)
+                              const u64 *__restrict__ hmont, const u64 *__restrict__ dmod,
+                              const u64 *__restrict__ dmodp, const double *__restrict__ inv_q)
 {
     extern __shared__ u64 sh[];   // [ns][M] constants
     const int j = blockIdx.y, it = blockIdx.z;
@@ -71,15 +74,20 @@ __global__ void k_modup_bconv(int ell, int L, int K, int alpha, int M, int n, co
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     u64 y[16];
+    double f = 0.0;
     const u64 *src = coef + it * coef_stride;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (i < ns) {
             const u64 q = mc[lo + i].q;
             y[i] = mul_shoup(src[(size_t)(lo + i) * n + k], __ldg(hinv + row0 + i), __ldg(hinvp + row0 + i), q);
+            f = fma((double)y[i], __ldg(inv_q + lo + i), f);
         }
     }
+    const u64 v = (u64)rint(f);
     const int next = ell + K;
+    const u64 *dm = dmod + (size_t)(hi - 1) * M;
+    const u64 *dmp = dmodp + (size_t)(hi - 1) * M;
     u64 *dst = ext + it * ext_stride + (size_t)j * next * n;
     for (int t = 0; t < next; ++t) {
         if (t >= lo && t < hi) continue;
@@ -89,7 +97,8 @@ __global__ void k_modup_bconv(int ell, int L, int K, int alpha, int M, int n, co
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             if (i < ns) mac_wide(acc, y[i], sh[i * M + gm]);
-        dst[(size_t)t * n + k] = redc(acc, m.q, m.qneg_inv);
+        const u64 r = redc(acc, m.q, m.qneg_inv);
+        dst[(size_t)t * n + k] = sub_mod(r, mul_shoup(v, __ldg(dm + gm), __ldg(dmp + gm), m.q), m.q);
     }
 }
 
@@ -147,11 +156,20 @@ __global__ void k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *
     }
 }
 
-// ModDown basis conversion P -> Q_ell: in = acc (coefficient rep. on the P
-// limbs), out conv [items][2][ell][n].
+// ModDown basis conversion P -> Q_ell of the CENTRED representative of the
+// accumulator modulo P: with y_k = [acc_k (P/p_k)^{-1}]_{p_k},
+//   sum_k y_k (P/p_k) = (acc mod P) + u P,  u = floor(sum_k y_k / p_k),
+// and v = round(sum_k y_k / p_k) (fma chain over k ascending, 1/p_k as a
+// correctly rounded double) replaces u, so
+// conv = sum_k y_k (P/p_k) - v P lies in [-P/2, P/2) and the final
+// (acc - conv) / P is acc / P rounded to nearest: a zero-mean error
+// (Halevi-Polyakov-Shoup floating-point correction, CT-RSA 2019).
+// in = acc (coefficient rep. on the P limbs), out conv [items][2][ell][n].
 __global__ void k_moddown_bconv(int ell, int L, int K, int M, int n, const u64 *acc, long long acc_stride,
                                 u64 *conv, const ModConst *__restrict__ mc, const u64 *__restrict__ hinv,
-                                const u64 *__restrict__ hinvp, const u64 *__restrict__ hmont)
+                                const u64 *__restrict__ hinvp, const u64 *__restrict__ hmont,
+                                const u64 *__restrict__ pmod, const u64 *__restrict__ pmodp,
+                                const double *__restrict__ inv_q)
 {
     extern __shared__ u64 sh[];   // [K][M]
     for (int x = threadIdx.x; x < K * M; x += blockDim.x) sh[x] = hmont[x];
@@ -162,9 +180,15 @@ __global__ void k_moddown_bconv(int ell, int L, int K, int M, int n, const u64 *
     const int next = ell + K;
     const u64 *src = acc + it * acc_stride + ((size_t)b * next + ell) * n;
     u64 y[16];
+    double f = 0.0;
 #pragma unroll
     for (int i = 0; i < 16; ++i)
-        if (i < K) y[i] = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), mc[L + i].q);
+        if (i < K) {
+            const u64 p = mc[L + i].q;
+            y[i] = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), p);
+            f = fma((double)y[i], __ldg(inv_q + L + i), f);
+        }
+    const u64 v = (u64)rint(f);
     u64 *dst = conv + ((size_t)it * 2 + b) * ell * n;
     for (int t = 0; t < ell; ++t) {
         const ModConst m = mc[t];
@@ -172,7 +196,8 @@ __global__ void k_moddown_bconv(int ell, int L, int K, int M, int n, const u64 *
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             if (i < K) mac_wide(a, y[i], sh[i * M + t]);
-        dst[(size_t)t * n + k] = redc(a, m.q, m.qneg_inv);
+        const u64 r = redc(a, m.q, m.qneg_inv);
+        dst[(size_t)t * n + k] = sub_mod(r, mul_shoup(v, __ldg(pmod + t), __ldg(pmodp + t), m.q), m.q);
     }
 }
 
@@ -518,7 +543,8 @@ void modup_bconv(Ctx &ctx, int items, int ell, const u64 *coef, long long coef_s
         cudaEvent_t t0_ = prof_begin(ctx);
         k_modup_bconv<<<grid_n(ctx.n, beta, items), kT, smem, ctx.stream>>>(
             ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, coef, coef_stride, ext, ext_stride, ctx.dt.mc,
-            ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_mont);
+            ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_mont, ctx.dt.mu_dmod, ctx.dt.mu_dmod_p,
+            ctx.dt.inv_q);
         prof_end(ctx, t0_, K_MODUP, 8.0 * ctx.n * items * beta * (ell + ctx.K), modup_macs(ctx, ell) * items, "modup bconv");
     }
 }
@@ -582,7 +608,7 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
         cudaEvent_t t0_ = prof_begin(ctx);
         k_moddown_bconv<<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
             ell, ctx.L, ctx.K, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv,
-            ctx.dt.md_hat_inv_p, ctx.dt.md_hat_mont);
+            ctx.dt.md_hat_inv_p, ctx.dt.md_hat_mont, ctx.dt.md_pmod, ctx.dt.md_pmod_p, ctx.dt.inv_q);
         prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");
     }
     LimbMap qm;

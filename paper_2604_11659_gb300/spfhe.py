@@ -64,6 +64,7 @@ _SIGS = [
     ("spfhe_prof_enable", ctypes.c_int, [handle, ctypes.c_int]),
     ("spfhe_prof_read", ctypes.c_int, [handle, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), c_dblp, c_dblp, c_dblp]),
     ("spfhe_prof_classes", ctypes.c_int, []),
+    ("spfhe_prof_keyswitch", ctypes.c_int, [handle, ctypes.POINTER(ctypes.c_uint64), c_dblp]),
     ("spfhe_prof_class_name", ctypes.c_char_p, [ctypes.c_int]),
     ("spfhe_keygen", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
     ("spfhe_keys_import", ctypes.c_int, [handle, c_i64p, c_u64p, ctypes.c_size_t, c_i32p,
@@ -204,6 +205,13 @@ def spfhe_prof_read(ctx, cls: int) -> dict:
     wk = ctypes.c_double()
     _check(lib().spfhe_prof_read(ctx, cls, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(wk)))
     return {"launches": int(la.value), "ms": ms.value, "bytes": by.value, "work": wk.value}
+
+
+def spfhe_prof_keyswitch(ctx):
+    calls = ctypes.c_uint64()
+    by = ctypes.c_double()
+    _check(lib().spfhe_prof_keyswitch(ctx, ctypes.byref(calls), ctypes.byref(by)))
+    return int(calls.value), by.value
 
 
 def spfhe_prof_all(ctx) -> dict:

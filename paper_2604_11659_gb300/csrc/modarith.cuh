@@ -29,9 +29,12 @@ __device__ __forceinline__ void add_wide(U128 &acc, U128 x)
     acc.lo = lo;
 }
 
+// acc += a * b (128-bit), one carry chain
 __device__ __forceinline__ void mac_wide(U128 &acc, u64 a, u64 b)
 {
-    add_wide(acc, mul_wide(a, b));
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
 }
 
 // x in [0, 2q) -> [0, q)
@@ -61,9 +64,14 @@ __device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
 // Montgomery reduction of T = (hi, lo) < q * 2^64: returns T * 2^-64 mod q in [0, q)
 __device__ __forceinline__ u64 redc(U128 t, u64 q, u64 qneg_inv)
 {
-    u64 m = t.lo * qneg_inv;
-    u64 mh = __umul64hi(m, q);
-    u64 r = t.hi + mh + (t.lo != 0 ? 1ull : 0ull);
+    // (t + m q) / 2^64 with m = t.lo * (-q^{-1}): the low word cancels, its
+    // carry is taken from the same add chain
+    const u64 m = t.lo * qneg_inv;
+    u64 r, dummy;
+    asm("mad.lo.cc.u64 %0, %2, %3, %4;\n\tmadc.hi.u64 %1, %2, %3, %5;"
+        : "=l"(dummy), "=l"(r)
+        : "l"(m), "l"(q), "l"(t.lo), "l"(t.hi));
+    (void)dummy;
     return csub(r, q);
 }
 

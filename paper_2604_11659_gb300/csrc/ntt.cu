@@ -194,6 +194,315 @@ __global__ void __launch_bounds__(kThreads) k_inv_a(NttArgs a, const ModConst *_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident radix-16 transforms for n >= 2^12.
+//
+// A pass of P stages (6 <= P <= 9) runs on tiles of 2^P elements (pass A: one
+// column of 2^P rows, stride n >> P; pass B: 2^P contiguous elements).  A CTA
+// of 256 threads owns 4096 elements (4096 >> P tiles); every thread holds 16
+// elements of one tile in registers.  Round r covers the pass-local stages
+// [4r, 4r + Q), Q = min(4, P - 4r): the 16 registers hold 2^(4-Q) groups of
+// 2^Q elements whose tile indices differ only in the Q bits that these stages
+// pair, so each round is 4 (or Q) butterfly stages without any exchange;
+// rounds are separated by one shared-memory transpose.
+//   round r < last (Q = 4, a0 = P - 4r - 4 > 0):
+//       j = (t & (2^a0 - 1)) | (i << a0) | ((t >> a0) << (a0 + 4))
+//   last round (bit 0 is paired):  j = 16 t + i
+// (t = thread index within its tile, i = register index).
+// ---------------------------------------------------------------------------
+constexpr int kElems = 4096;
+
+template <int P, int RND> __device__ __forceinline__ int r16_index(int t, int i)
+{
+    constexpr int s0 = 4 * RND;
+    constexpr int Q = (P - s0) < 4 ? (P - s0) : 4;
+    constexpr int a0 = P - s0 - Q;
+    if constexpr (a0 == 0) {
+        return (t << 4) | i;
+    } else {
+        return (t & ((1 << a0) - 1)) | (i << a0) | ((t >> a0) << (a0 + 4));
+    }
+}
+
+template <int P, int RND> constexpr int r16_q() { return (P - 4 * RND) < 4 ? (P - 4 * RND) : 4; }
+
+// twiddle index of the butterfly whose lower element is tile index j at
+// pass-local stage ls: group G = j >> (P - ls); pass A (stage0 = 0):
+// 2^ls + G; pass B (stage0 = PA, tile b): 2^(PA + ls) + (b << ls) + G.
+template <int P> __device__ __forceinline__ int r16_tw(int j, int ls, int stage0, int btile)
+{
+    return (1 << (stage0 + ls)) + (btile << ls) + (j >> (P - ls));
+}
+
+// Harvey's lazy butterflies: forward values stay in [0, 4q) (x is brought to
+// [0, 2q) first, w*y is taken in [0, 2q)), inverse values in [0, 2q); only
+// the last pass reduces to [0, q).  Needs 4q < 2^64.
+template <int P, int RND>
+__device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const u64 *__restrict__ w,
+                                              const u64 *__restrict__ wp, u64 q, int stage0, int btile)
+{
+    constexpr int Q = r16_q<P, RND>();
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+        const int half = 1 << (Q - 1 - l);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i & half) continue;
+            const int j = r16_index<P, RND>(t, i);
+            const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
+            const u64 W = __ldg(w + ti), Wp = __ldg(wp + ti);
+            const u64 x = csub(v[i], q2);
+            const u64 y = mul_shoup_lazy(v[i + half], W, Wp, q);
+            v[i] = x + y;
+            v[i + half] = x - y + q2;
+        }
+    }
+}
+
+template <int P, int RND>
+__device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const u64 *__restrict__ w,
+                                              const u64 *__restrict__ wp, u64 q, int stage0, int btile)
+{
+    constexpr int Q = r16_q<P, RND>();
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int l = Q - 1; l >= 0; --l) {
+        const int half = 1 << (Q - 1 - l);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i & half) continue;
+            const int j = r16_index<P, RND>(t, i);
+            const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
+            const u64 W = __ldg(w + ti), Wp = __ldg(wp + ti);
+            const u64 x = v[i], y = v[i + half];
+            v[i] = csub(x + y, q2);
+            v[i + half] = mul_shoup_lazy(x - y + q2, W, Wp, q);
+        }
+    }
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q) { return csub(csub(x, 2 * q), q); }
+
+// shared-memory slot of tile element j (pass B layout; pad one word per 16)
+template <int P> __device__ __forceinline__ int r16_slot_b(int tile, int j)
+{
+    return tile * ((1 << P) + (1 << (P - 4))) + j + (j >> 4);
+}
+// pass A layout: [row][column], 8 words of padding per 16 rows
+template <int P> __device__ __forceinline__ int r16_slot_a(int col, int row)
+{
+    return row * (kElems >> P) + col + ((row >> 4) << 3);
+}
+template <int P> constexpr int r16_smem_words_a() { return kElems + (((1 << P) >> 4) << 3); }
+template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4); }
+
+template <int P>
+__global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__restrict__ mc,
+                                                 const u64 *__restrict__ tw, const u64 *__restrict__ twp, int log_n)
+{
+    __shared__ u64 sm[r16_smem_words_a<P>()];
+    constexpr int TPC = kElems >> P;   // columns per CTA
+    constexpr int R = (P + 3) / 4;
+    const int n = 1 << log_n;
+    int mi;
+    u64 *p = limb_ptr(a, n, mi);
+    const u64 q = mc[mi].q;
+    const u64 *w = tw + (size_t)mi * n, *wp = twp + (size_t)mi * n;
+    const int lg_ncols = log_n - P;
+    const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
+    const int gcol = blockIdx.x * TPC + col;
+    u64 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
+    r16_fwd_round<P, 0>(v, t, w, wp, q, 0, 0);
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))];
+        r16_fwd_round<P, 1>(v, t, w, wp, q, 0, 0);
+    }
+    if constexpr (R > 2) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 2>(t, i))];
+        r16_fwd_round<P, 2>(v, t, w, wp, q, 0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__restrict__ mc,
+                                                 const u64 *__restrict__ tw, const u64 *__restrict__ twp, int log_n,
+                                                 int PA)
+{
+    __shared__ u64 sm[r16_smem_words_b<P>()];
+    constexpr int TPT = 1 << (P - 4);  // threads per tile
+    constexpr int R = (P + 3) / 4;
+    const int n = 1 << log_n;
+    int mi;
+    u64 *p = limb_ptr(a, n, mi);
+    const u64 q = mc[mi].q;
+    const u64 *w = tw + (size_t)mi * n, *wp = twp + (size_t)mi * n;
+    const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
+    const size_t e0 = (size_t)blockIdx.x * kElems;
+    const int btile = (int)(e0 >> P) + tile;
+    u64 *tp = p + e0 + ((size_t)tile << P);
+    u64 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = tp[r16_index<P, 0>(t, i)];
+    r16_fwd_round<P, 0>(v, t, w, wp, q, PA, btile);
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
+        r16_fwd_round<P, 1>(v, t, w, wp, q, PA, btile);
+    }
+    if constexpr (R > 2) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
+        r16_fwd_round<P, 2>(v, t, w, wp, q, PA, btile);
+    }
+    // the last round holds 16 contiguous elements per thread: stage through
+    // shared memory so the global stores are coalesced
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
+    __syncthreads();
+    for (int x = threadIdx.x; x < kElems; x += 256) p[e0 + x] = reduce4(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__restrict__ mc,
+                                                 const u64 *__restrict__ itw, const u64 *__restrict__ itwp,
+                                                 int log_n, int PA)
+{
+    __shared__ u64 sm[r16_smem_words_b<P>()];
+    constexpr int TPT = 1 << (P - 4);
+    constexpr int R = (P + 3) / 4;
+    const int n = 1 << log_n;
+    int mi;
+    u64 *p = limb_ptr(a, n, mi);
+    const u64 q = mc[mi].q;
+    const u64 *w = itw + (size_t)mi * n, *wp = itwp + (size_t)mi * n;
+    const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
+    const size_t e0 = (size_t)blockIdx.x * kElems;
+    const int btile = (int)(e0 >> P) + tile;
+    for (int x = threadIdx.x; x < kElems; x += 256) sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = p[e0 + x];
+    __syncthreads();
+    u64 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
+    r16_inv_round<P, R - 1>(v, t, w, wp, q, PA, btile);
+    if constexpr (R > 2) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
+        r16_inv_round<P, R - 2>(v, t, w, wp, q, PA, btile);
+    }
+    if constexpr (R > 1) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
+        r16_inv_round<P, 0>(v, t, w, wp, q, PA, btile);
+    }
+    u64 *tp = p + e0 + ((size_t)tile << P);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tp[r16_index<P, 0>(t, i)] = v[i];
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__restrict__ mc,
+                                                 const u64 *__restrict__ itw, const u64 *__restrict__ itwp,
+                                                 int log_n)
+{
+    __shared__ u64 sm[r16_smem_words_a<P>()];
+    constexpr int TPC = kElems >> P;
+    constexpr int R = (P + 3) / 4;
+    const int n = 1 << log_n;
+    int mi;
+    u64 *p = limb_ptr(a, n, mi);
+    const ModConst m = mc[mi];
+    const u64 q = m.q;
+    const u64 *w = itw + (size_t)mi * n, *wp = itwp + (size_t)mi * n;
+    const int lg_ncols = log_n - P;
+    const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
+    const int gcol = blockIdx.x * TPC + col;
+    u64 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol];
+    r16_inv_round<P, R - 1>(v, t, w, wp, q, 0, 0);
+    if constexpr (R > 2) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, R - 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, R - 2>(t, i))];
+        r16_inv_round<P, R - 2>(v, t, w, wp, q, 0, 0);
+        __syncthreads();
+    }
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))];
+        r16_inv_round<P, 0>(v, t, w, wp, q, 0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = mul_shoup(v[i], m.n_inv, m.n_inv_p, q);
+}
+
+template <int P> struct R16Launch {
+    static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
+    {
+        k_fwd16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw, c.dt.twp, c.log_n);
+    }
+    static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
+    {
+        k_fwd16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw, c.dt.twp, c.log_n, PA);
+    }
+    static void inv_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
+    {
+        k_inv16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw, c.dt.itwp, c.log_n);
+    }
+    static void inv_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
+    {
+        k_inv16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw, c.dt.itwp, c.log_n, PA);
+    }
+};
+
+template <typename F> void r16_dispatch(int P, F &&f)
+{
+    switch (P) {
+    case 6: f(R16Launch<6>{}); break;
+    case 7: f(R16Launch<7>{}); break;
+    case 8: f(R16Launch<8>{}); break;
+    case 9: f(R16Launch<9>{}); break;
+    default: throw Error(SPFHE_EINVAL, "no radix-16 pass for this size");
+    }
+}
+
 struct Geometry {
     int PA, lg_cols, lgC, lgE;
     size_t smem_a, smem_b;
@@ -242,16 +551,32 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
     if (map.nl <= 0 || b.items <= 0) return;
     Geometry g = geometry(ctx.log_n);
     NttArgs a{b.base, b.stride, b.ids, map};
+    const int cls = ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD;
+    if (ctx.log_n >= 12) {
+        const int PA = ctx.log_n / 2, PB = ctx.log_n - PA;
+        dim3 grid(ctx.n / kElems, map.nl, b.items);
+        {
+            cudaEvent_t t0_ = prof_begin(ctx);
+            r16_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, a, ctx); });
+            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items, "ntt fwd A");
+        }
+        {
+            cudaEvent_t t0_ = prof_begin(ctx);
+            r16_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, a, ctx, PA); });
+            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PB * map.nl * b.items, "ntt fwd B");
+        }
+        return;
+    }
     dim3 ga(g.grid_a, map.nl, b.items), gb(g.grid_b, map.nl, b.items);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
+        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
+        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
     }
 }
 
@@ -261,16 +586,32 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
     if (map.nl <= 0 || b.items <= 0) return;
     Geometry g = geometry(ctx.log_n);
     NttArgs a{b.base, b.stride, b.ids, map};
+    const int cls = ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV;
+    if (ctx.log_n >= 12) {
+        const int PA = ctx.log_n / 2, PB = ctx.log_n - PA;
+        dim3 grid(ctx.n / kElems, map.nl, b.items);
+        {
+            cudaEvent_t t0_ = prof_begin(ctx);
+            r16_dispatch(PB, [&](auto L) { decltype(L)::inv_b(grid, ctx.stream, a, ctx, PA); });
+            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PB * map.nl * b.items, "ntt inv B");
+        }
+        {
+            cudaEvent_t t0_ = prof_begin(ctx);
+            r16_dispatch(PA, [&](auto L) { decltype(L)::inv_a(grid, ctx.stream, a, ctx); });
+            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items, "ntt inv A");
+        }
+        return;
+    }
     dim3 ga(g.grid_a, map.nl, b.items), gb(g.grid_b, map.nl, b.items);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
+        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
+        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
     }
 }
 

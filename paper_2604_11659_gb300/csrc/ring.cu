@@ -2,6 +2,7 @@
 // Layouts: a polynomial at level ell is [ell][n] u64 (limb-major), a
 // ciphertext [2][ell][n]; batches place items `stride` words apart.
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -58,47 +59,46 @@ __global__ void k_automorph(int polys, int ell, int log_n, const u64 *const *in,
 //   y_i = [x_i (D/q_i)^{-1}]_{q_i},  v = round(sum_i y_i / q_i) (fma chain),
 //   out_t = sum_i y_i (D/q_i) - v D  mod m_t.
 // Extended limb t < ell is q_t, t >= ell is p_{t-ell} (modulus L + t - ell).
-__global__ void k_modup_bconv(int ell, int L, int K, int alpha, int M, int n, const u64 *coef, long long coef_stride,
-                              u64 *ext, long long ext_stride, const ModConst *__restrict__ mc,
-                              const u64 *__restrict__ hinv, const u64 *__restrict__ hinvp,
-                              const u64 *__restrict__ hmont, const u64 *__restrict__ dmod,
-                              const u64 *__restrict__ dmodp, const double *__restrict__ inv_q)
+template <int NS>
+__global__ void __launch_bounds__(256) k_modup_bconv(int digit0, int ell, int L, int K, int alpha, int M, int n,
+                                                     const u64 *coef,
+                                                     long long coef_stride, u64 *ext, long long ext_stride,
+                                                     const ModConst *__restrict__ mc, const u64 *__restrict__ hinv,
+                                                     const u64 *__restrict__ hinvp, const u64 *__restrict__ hmont,
+                                                     const u64 *__restrict__ dmod, const u64 *__restrict__ dmodp,
+                                                     const double *__restrict__ inv_q)
 {
-    extern __shared__ u64 sh[];   // [ns][M] constants
-    const int j = blockIdx.y, it = blockIdx.z;
-    const int lo = j * alpha, hi = min(lo + alpha, ell);
-    const int ns = hi - lo;
+    extern __shared__ u64 sh[];   // [NS][M] constants
+    const int j = digit0 + blockIdx.y, it = blockIdx.z;
+    const int lo = j * alpha, hi = lo + NS;
     const size_t row0 = (size_t)(hi - 1) * alpha;
-    for (int x = threadIdx.x; x < ns * M; x += blockDim.x) sh[x] = hmont[row0 * M + x];
+    for (int x = threadIdx.x; x < NS * M; x += blockDim.x) sh[x] = hmont[row0 * M + x];
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    u64 y[16];
+    u64 y[NS];
     double f = 0.0;
     const u64 *src = coef + it * coef_stride;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if (i < ns) {
-            const u64 q = mc[lo + i].q;
-            y[i] = mul_shoup(src[(size_t)(lo + i) * n + k], __ldg(hinv + row0 + i), __ldg(hinvp + row0 + i), q);
-            f = fma((double)y[i], __ldg(inv_q + lo + i), f);
-        }
+    for (int i = 0; i < NS; ++i) {
+        const u64 q = mc[lo + i].q;
+        y[i] = mul_shoup(src[(size_t)(lo + i) * n + k], __ldg(hinv + row0 + i), __ldg(hinvp + row0 + i), q);
+        f = fma((double)y[i], __ldg(inv_q + lo + i), f);
     }
     const u64 v = (u64)rint(f);
     const int next = ell + K;
     const u64 *dm = dmod + (size_t)(hi - 1) * M;
     const u64 *dmp = dmodp + (size_t)(hi - 1) * M;
-    u64 *dst = ext + it * ext_stride + (size_t)j * next * n;
+    u64 *dst = ext + it * ext_stride + (size_t)j * next * n + k;
     for (int t = 0; t < next; ++t) {
         if (t >= lo && t < hi) continue;
         const int gm = t < ell ? t : L + (t - ell);
-        const ModConst m = mc[gm];
+        const u64 q = mc[gm].q, qi = mc[gm].qneg_inv;
         U128 acc = {0, 0};
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (i < ns) mac_wide(acc, y[i], sh[i * M + gm]);
-        const u64 r = redc(acc, m.q, m.qneg_inv);
-        dst[(size_t)t * n + k] = sub_mod(r, mul_shoup(v, __ldg(dm + gm), __ldg(dmp + gm), m.q), m.q);
+        for (int i = 0; i < NS; ++i) mac_wide(acc, y[i], sh[i * M + gm]);
+        const u64 r = redc(acc, q, qi);
+        dst[(size_t)t * n] = sub_mod(r, mul_shoup(v, __ldg(dm + gm), __ldg(dmp + gm), q), q);
     }
 }
 
@@ -115,44 +115,56 @@ struct IpGroups {
     IpGroup g[kMaxIpGroups];
 };
 
-__global__ void k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *const *in, const u64 *ext,
-                     long long ext_stride, IpGroups groups, u64 *acc, long long acc_stride,
-                     const ModConst *__restrict__ mc)
+// BETA = number of digits at this level (compile-time, so the per-thread key
+// values stay in registers); BETA = 0 selects a generic loop for larger counts.
+template <int BETA>
+__global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *const *in,
+                                            const u64 *ext, long long ext_stride, IpGroups groups, u64 *acc,
+                                            long long acc_stride, const ModConst *__restrict__ mc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int t = blockIdx.y;
     const IpGroup gr = groups.g[blockIdx.z];
     const int next = ell + K;
-    const int beta = (ell + alpha - 1) / alpha;
     const int gm = t < ell ? t : L + (t - ell);
     const ModConst m = mc[gm];
-    u64 k0[16], k1[16];
+    // digit holding limb t (t < ell), -1 for special-prime limbs
+    const int own = t < ell ? t / alpha : -1;
+    if constexpr (BETA > 0) {
+        u64 k0[BETA], k1[BETA];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (j < beta) {
+        for (int j = 0; j < BETA; ++j) {
             k0[j] = __ldg(gr.key + (((size_t)j * 2 + 0) * M + gm) * n + k);
             k1[j] = __ldg(gr.key + (((size_t)j * 2 + 1) * M + gm) * n + k);
         }
-    }
-    for (int it = gr.first; it < gr.first + gr.count; ++it) {
-        U128 a0 = {0, 0}, a1 = {0, 0};
+        for (int it = gr.first; it < gr.first + gr.count; ++it) {
+            U128 a0 = {0, 0}, a1 = {0, 0};
+            const u64 *e_it = ext + it * ext_stride + (size_t)t * n + k;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (j < beta) {
-                const int lo = j * alpha;
-                u64 e;
-                if (t >= lo && t < lo + alpha && t < ell)
-                    e = in[it][(size_t)t * n + k];
-                else
-                    e = ext[it * ext_stride + ((size_t)j * next + t) * n + k];
+            for (int j = 0; j < BETA; ++j) {
+                const u64 e = (j == own) ? in[it][(size_t)t * n + k] : e_it[(size_t)j * next * n];
                 mac_wide(a0, e, k0[j]);
                 mac_wide(a1, e, k1[j]);
             }
+            u64 *o = acc + it * acc_stride;
+            o[(size_t)t * n + k] = redc(a0, m.q, m.qneg_inv);
+            o[((size_t)next + t) * n + k] = redc(a1, m.q, m.qneg_inv);
         }
-        u64 *o = acc + it * acc_stride;
-        o[(size_t)t * n + k] = redc(a0, m.q, m.qneg_inv);
-        o[((size_t)next + t) * n + k] = redc(a1, m.q, m.qneg_inv);
+    } else {
+        const int beta = (ell + alpha - 1) / alpha;
+        for (int it = gr.first; it < gr.first + gr.count; ++it) {
+            U128 a0 = {0, 0}, a1 = {0, 0};
+            for (int j = 0; j < beta; ++j) {
+                const u64 e = (j == own) ? in[it][(size_t)t * n + k]
+                                         : ext[it * ext_stride + ((size_t)j * next + t) * n + k];
+                mac_wide(a0, e, __ldg(gr.key + (((size_t)j * 2 + 0) * M + gm) * n + k));
+                mac_wide(a1, e, __ldg(gr.key + (((size_t)j * 2 + 1) * M + gm) * n + k));
+            }
+            u64 *o = acc + it * acc_stride;
+            o[(size_t)t * n + k] = redc(a0, m.q, m.qneg_inv);
+            o[((size_t)next + t) * n + k] = redc(a1, m.q, m.qneg_inv);
+        }
     }
 }
 
@@ -165,39 +177,38 @@ __global__ void k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *
 // (acc - conv) / P is acc / P rounded to nearest: a zero-mean error
 // (Halevi-Polyakov-Shoup floating-point correction, CT-RSA 2019).
 // in = acc (coefficient rep. on the P limbs), out conv [items][2][ell][n].
-__global__ void k_moddown_bconv(int ell, int L, int K, int M, int n, const u64 *acc, long long acc_stride,
-                                u64 *conv, const ModConst *__restrict__ mc, const u64 *__restrict__ hinv,
-                                const u64 *__restrict__ hinvp, const u64 *__restrict__ hmont,
-                                const u64 *__restrict__ pmod, const u64 *__restrict__ pmodp,
-                                const double *__restrict__ inv_q)
+template <int KK>
+__global__ void __launch_bounds__(256) k_moddown_bconv(int ell, int L, int M, int n, const u64 *acc,
+                                                       long long acc_stride, u64 *conv, const ModConst *__restrict__ mc,
+                                                       const u64 *__restrict__ hinv, const u64 *__restrict__ hinvp,
+                                                       const u64 *__restrict__ hmont, const u64 *__restrict__ pmod,
+                                                       const u64 *__restrict__ pmodp, const double *__restrict__ inv_q)
 {
-    extern __shared__ u64 sh[];   // [K][M]
-    for (int x = threadIdx.x; x < K * M; x += blockDim.x) sh[x] = hmont[x];
+    extern __shared__ u64 sh[];   // [KK][M]
+    for (int x = threadIdx.x; x < KK * M; x += blockDim.x) sh[x] = hmont[x];
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int b = blockIdx.y, it = blockIdx.z;
-    const int next = ell + K;
+    const int next = ell + KK;
     const u64 *src = acc + it * acc_stride + ((size_t)b * next + ell) * n;
-    u64 y[16];
+    u64 y[KK];
     double f = 0.0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        if (i < K) {
-            const u64 p = mc[L + i].q;
-            y[i] = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), p);
-            f = fma((double)y[i], __ldg(inv_q + L + i), f);
-        }
+    for (int i = 0; i < KK; ++i) {
+        const u64 p = mc[L + i].q;
+        y[i] = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), p);
+        f = fma((double)y[i], __ldg(inv_q + L + i), f);
+    }
     const u64 v = (u64)rint(f);
-    u64 *dst = conv + ((size_t)it * 2 + b) * ell * n;
+    u64 *dst = conv + ((size_t)it * 2 + b) * ell * n + k;
     for (int t = 0; t < ell; ++t) {
-        const ModConst m = mc[t];
+        const u64 q = mc[t].q, qi = mc[t].qneg_inv;
         U128 a = {0, 0};
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (i < K) mac_wide(a, y[i], sh[i * M + t]);
-        const u64 r = redc(a, m.q, m.qneg_inv);
-        dst[(size_t)t * n + k] = sub_mod(r, mul_shoup(v, __ldg(pmod + t), __ldg(pmodp + t), m.q), m.q);
+        for (int i = 0; i < KK; ++i) mac_wide(a, y[i], sh[i * M + t]);
+        const u64 r = redc(a, q, qi);
+        dst[(size_t)t * n] = sub_mod(r, mul_shoup(v, __ldg(pmod + t), __ldg(pmodp + t), q), q);
     }
 }
 
@@ -504,15 +515,6 @@ __global__ void k_mul_poly(int n, const u64 *a, const u64 *b, u64 *out, const Mo
 
 }  // namespace
 
-static double modup_macs(const Ctx &ctx, int ell)
-{
-    double macs = 0;
-    for (int lo = 0; lo < ell; lo += ctx.alpha) {
-        const int d = std::min(ctx.alpha, ell - lo);
-        macs += (double)d * (ell + ctx.K - d);
-    }
-    return macs * ctx.n;
-}
 
 void tensor(Ctx &ctx, int items, int ell, const u64 *const *pa, const u64 *const *pb, u64 *d)
 {
@@ -534,19 +536,51 @@ void automorph(Ctx &ctx, int items, int polys, int ell, const u64 *const *in, lo
     }
 }
 
+template <typename F> static void ns_dispatch(int ns, F &&f)
+{
+    switch (ns) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 9: f(std::integral_constant<int, 9>{}); break;
+    case 10: f(std::integral_constant<int, 10>{}); break;
+    case 11: f(std::integral_constant<int, 11>{}); break;
+    case 12: f(std::integral_constant<int, 12>{}); break;
+    case 13: f(std::integral_constant<int, 13>{}); break;
+    case 14: f(std::integral_constant<int, 14>{}); break;
+    case 15: f(std::integral_constant<int, 15>{}); break;
+    default: throw Error(SPFHE_EPARAM, "digit width out of range");
+    }
+}
+
 void modup_bconv(Ctx &ctx, int items, int ell, const u64 *coef, long long coef_stride, u64 *ext,
                  long long ext_stride)
 {
     const int beta = (ell + ctx.alpha - 1) / ctx.alpha;
-    const size_t smem = (size_t)ctx.alpha * ctx.M * sizeof(u64);
-    {
+    const int full = ell / ctx.alpha;            // digits of width alpha
+    const int last = ell - full * ctx.alpha;     // width of a truncated last digit (0: none)
+    auto launch = [&](int digit0, int ndig, int ns) {
+        const size_t smem = (size_t)ns * ctx.M * sizeof(u64);
+        const dim3 grid((ctx.n + kT - 1) / kT, ndig, items);
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_modup_bconv<<<grid_n(ctx.n, beta, items), kT, smem, ctx.stream>>>(
-            ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, coef, coef_stride, ext, ext_stride, ctx.dt.mc,
-            ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_mont, ctx.dt.mu_dmod, ctx.dt.mu_dmod_p,
-            ctx.dt.inv_q);
-        prof_end(ctx, t0_, K_MODUP, 8.0 * ctx.n * items * beta * (ell + ctx.K), modup_macs(ctx, ell) * items, "modup bconv");
-    }
+        ns_dispatch(ns, [&](auto NS) {
+            k_modup_bconv<decltype(NS)::value><<<grid, kT, smem, ctx.stream>>>(
+                digit0, ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, coef, coef_stride, ext, ext_stride, ctx.dt.mc,
+                ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_mont, ctx.dt.mu_dmod, ctx.dt.mu_dmod_p,
+                ctx.dt.inv_q);
+        });
+        double macs = 0;
+        for (int d = digit0; d < digit0 + ndig; ++d) macs += (double)ns * (ell + ctx.K - ns);
+        prof_end(ctx, t0_, K_MODUP, 8.0 * ctx.n * items * ndig * (ell + ctx.K), macs * ctx.n * items, "modup bconv");
+    };
+    if (full > 0) launch(0, full, ctx.alpha);
+    if (last > 0) launch(full, 1, last);
+    (void)beta;
 }
 
 LimbMap modup_ntt_map(const Ctx &ctx, int ell)
@@ -582,8 +616,19 @@ void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const 
         const double beta_ip = (ell + ctx.alpha - 1) / ctx.alpha;
         {
             cudaEvent_t t0_ = prof_begin(ctx);
-            k_ip<<<grid_n(ctx.n, ell + ctx.K, cnt), kT, 0, ctx.stream>>>(ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, in,
-                                                                        ext, ext_stride, hg, acc, acc_stride, ctx.dt.mc);
+            const dim3 grid = grid_n(ctx.n, ell + ctx.K, cnt);
+#define SPFHE_IP(BB) k_ip<BB><<<grid, kT, 0, ctx.stream>>>(ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, in, ext, \
+                                                           ext_stride, hg, acc, acc_stride, ctx.dt.mc)
+            switch ((int)beta_ip) {
+            case 1: SPFHE_IP(1); break;
+            case 2: SPFHE_IP(2); break;
+            case 3: SPFHE_IP(3); break;
+            case 4: SPFHE_IP(4); break;
+            case 5: SPFHE_IP(5); break;
+            case 6: SPFHE_IP(6); break;
+            default: SPFHE_IP(0); break;
+            }
+#undef SPFHE_IP
             prof_end(ctx, t0_, K_IP, 8.0 * ctx.n * (ip_items * (beta_ip * (ell + ctx.K) + 2.0 * (ell + ctx.K)) + cnt * 2.0 * beta_ip * (ell + ctx.K)), 2.0 * ctx.n * ip_items * beta_ip * (ell + ctx.K), "ks inner product");
         }
     }
@@ -606,9 +651,11 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
     const size_t smem = (size_t)ctx.K * ctx.M * sizeof(u64);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_moddown_bconv<<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
-            ell, ctx.L, ctx.K, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv,
-            ctx.dt.md_hat_inv_p, ctx.dt.md_hat_mont, ctx.dt.md_pmod, ctx.dt.md_pmod_p, ctx.dt.inv_q);
+        ns_dispatch(ctx.K, [&](auto KK) {
+            k_moddown_bconv<decltype(KK)::value><<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
+                ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv, ctx.dt.md_hat_inv_p,
+                ctx.dt.md_hat_mont, ctx.dt.md_pmod, ctx.dt.md_pmod_p, ctx.dt.inv_q);
+        });
         prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");
     }
     LimbMap qm;

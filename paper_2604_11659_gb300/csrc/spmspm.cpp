@@ -292,7 +292,7 @@ void spmspm_ct_ct(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
                     }
                     tensor(ctx, m, L, rt.upload_vec(pa), rt.upload_vec(pb), D);
                     std::vector<KeyGroup> groups;
-                    const int gsz = 4;
+                    const int gsz = 8;
                     for (int i = 0; i < m; i += gsz) groups.push_back(KeyGroup{keys.relin, i, std::min(gsz, m - i)});
                     keyswitch_batch(ctx, m, L, rt.upload_vec(d2), groups, rt.upload_vec(dbase), nullptr, true, X, csL);
                     st.ks_relin += m;

@@ -67,11 +67,10 @@ __device__ __forceinline__ u64 redc(U128 t, u64 q, u64 qneg_inv)
     // (t + m q) / 2^64 with m = t.lo * (-q^{-1}): the low word cancels, its
     // carry is taken from the same add chain
     const u64 m = t.lo * qneg_inv;
-    u64 r, dummy;
-    asm("mad.lo.cc.u64 %0, %2, %3, %4;\n\tmadc.hi.u64 %1, %2, %3, %5;"
-        : "=l"(dummy), "=l"(r)
+    u64 r;
+    asm("{\n\t.reg .u64 lo_;\n\tmad.lo.cc.u64 lo_, %1, %2, %3;\n\tmadc.hi.u64 %0, %1, %2, %4;\n\t}"
+        : "=l"(r)
         : "l"(m), "l"(q), "l"(t.lo), "l"(t.hi));
-    (void)dummy;
     return csub(r, q);
 }
 

@@ -223,6 +223,24 @@ spfhe_status spfhe_add(spfhe_ctx *ctx, const spfhe_ct *a, const spfhe_ct *b, spf
 spfhe_status spfhe_ntt(spfhe_ctx *ctx, uint64_t *dev_limbs, uint32_t n_limbs, const int32_t *mod_idx,
                        int inverse);
 
+/* Rescale that allocates nothing (the paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory while they run, e.g.
+ * a process that owns a fixed GPU memory budget and hands the library
+ * pre-sized buffers).  Same result as spfhe_rescale, bit for bit.
+ * in:  device pointer to a ciphertext [2][level][n] (evaluation rep.);
+ * out: device pointer receiving [2][level-1][n]; must not overlap `in`.
+ * Both stay owned by the caller.  The call enqueues its work on the context
+ * stream and returns; synchronise before reading `out`.
+ * Scratch lives in a fixed 2 MiB device array (2 * 2^17 words) that every
+ * process loading the library reserves on each GPU it uses until exit; all
+ * calls on a GPU share it, so calls that overlap on the GPU (different
+ * streams) race on it.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  No
+ * cudaMalloc/cudaFree or other allocating routine is called.
+ * Errors: SPFHE_EINVAL (null pointer, ring needing more than the fixed
+ * scratch), SPFHE_ELEVEL (level < 2 or > L), SPFHE_ECUDA. */
+spfhe_status spfhe_rescale_noalloc(spfhe_ctx *ctx, const uint64_t *in, uint32_t level, uint64_t *out);
+
 /* ---- Alg. 1 planner ------------------------------------------------------ */
 /* Alg. 1's merge over every (i, j): returns the matches in Alg. 1 order as
  * (i, j, k, a_pos, b_pos) rows.  Call with out = NULL to get the count in

@@ -7,20 +7,9 @@
 #include "runtime.h"
 
 
-using namespace spfhe;
+#include "handles.h"
 
-struct spfhe_ctx {
-    Ctx c;
-};
-struct spfhe_keys {
-    Keys *k;
-};
-struct spfhe_ct {
-    Ct *c;
-};
-struct spfhe_pt {
-    Pt *p;
-};
+using namespace spfhe;
 
 namespace {
 thread_local std::string g_err;
@@ -90,6 +79,10 @@ void same_scale(double a, double b)
     if (std::fabs(a - b) > 1e-9 * std::fabs(a)) throw Error(SPFHE_ESCALE, "operand scales differ");
 }
 }  // namespace
+
+namespace spfhe {
+void set_last_error(const std::string &m) { g_err = m; }
+}  // namespace spfhe
 
 extern "C" {
 

@@ -134,6 +134,9 @@ void build_params(Ctx &ctx, const spfhe_params &p);
 void upload_tables(Ctx &ctx);
 void free_tables(Ctx &ctx);
 
+// message returned by spfhe_last_error() for the calling thread (abi.cpp)
+void set_last_error(const std::string &m);
+
 // ---- memory (memory.cpp) ----
 void *dev_alloc(Ctx &ctx, size_t bytes);
 void dev_free(Ctx &ctx, void *p);

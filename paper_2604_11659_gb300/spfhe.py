@@ -91,6 +91,7 @@ _SIGS = [
     ("spfhe_mul_plain", ctypes.c_int, [handle, handle, handle, ctypes.POINTER(handle)]),
     ("spfhe_add", ctypes.c_int, [handle, handle, handle, ctypes.POINTER(handle)]),
     ("spfhe_ntt", ctypes.c_int, [handle, ctypes.c_void_p, ctypes.c_uint32, c_i32p, ctypes.c_int]),
+    ("spfhe_rescale_noalloc", ctypes.c_int, [handle, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     ("spfhe_plan_matches", ctypes.c_int, [ctypes.POINTER(SparseMeta), ctypes.POINTER(SparseMeta), c_i32p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
     ("spfhe_sparse_matmul_ct_ct", ctypes.c_int, [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle),
@@ -358,6 +359,10 @@ def spfhe_add(ctx, a, b):
 def spfhe_ntt(ctx, dev_ptr: int, mod_idx, inverse: bool):
     mi = np.ascontiguousarray(mod_idx, dtype=np.int32)
     _check(lib().spfhe_ntt(ctx, ctypes.c_void_p(dev_ptr), mi.size, _i32(mi), int(inverse)))
+
+
+def spfhe_rescale_noalloc(ctx, in_dev_ptr: int, level: int, out_dev_ptr: int):
+    _check(lib().spfhe_rescale_noalloc(ctx, ctypes.c_void_p(in_dev_ptr), level, ctypes.c_void_p(out_dev_ptr)))
 
 
 def sparse_meta(indptr: np.ndarray, indices: np.ndarray, rows: int, cols: int) -> SparseMeta:

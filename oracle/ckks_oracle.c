@@ -16,7 +16,9 @@
  * Nothing here is blocked, fused or reordered for speed: each routine is the
  * definition of the operation, with a radix-2 NTT used as the polynomial
  * multiplication primitive (itself pinned against the O(n^2) definitions
- * or_ntt_direct and or_negacyclic_schoolbook by the tests).
+ * or_ntt_direct and or_negacyclic_schoolbook by the tests).  Loops over
+ * independent limbs may run on several OpenMP threads (OMP_NUM_THREADS);
+ * every limb is computed by the same code either way.
  */
 #include <math.h>
 #include <stdint.h>
@@ -367,7 +369,8 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
 
     for (int j = 0; j < beta; j++) {
         int lo = j * alpha, hi = (j + 1) * alpha < ell ? (j + 1) * alpha : ell;
-        /* ModUp of digit j */
+        /* ModUp of digit j (limbs are independent: parallel over t) */
+#pragma omp parallel for schedule(dynamic)
         for (int t = 0; t < n_ext; t++) {
             if (t >= lo && t < hi) {
                 memcpy(ext + t * ln, c + t * ln, sizeof(u64) * ln);
@@ -376,13 +379,16 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
             }
         }
         /* inner product with the key */
+#pragma omp parallel for collapse(2) schedule(dynamic)
         for (int b = 0; b < 2; b++) {
             for (int t = 0; t < n_ext; t++) {
                 int mi = ext_mod_index(P, ell, t);
                 const u64 *key = ksk + (((size_t)j * 2 + b) * (L + K) + mi) * ln;
-                or_polymul(ext + t * ln, key, prod, P->log_n, P->mods[mi], P->psis[mi]);
+                u64 *pr = (u64 *)malloc(sizeof(u64) * ln);
+                or_polymul(ext + t * ln, key, pr, P->log_n, P->mods[mi], P->psis[mi]);
                 for (int k = 0; k < n; k++)
-                    acc[b][t * ln + k] = addmod(acc[b][t * ln + k], prod[k], P->mods[mi]);
+                    acc[b][t * ln + k] = addmod(acc[b][t * ln + k], pr[k], P->mods[mi]);
+                free(pr);
             }
         }
     }
@@ -395,7 +401,9 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
     }
     u64 *conv = (u64 *)malloc(sizeof(u64) * ell * ln);
     for (int b = 0; b < 2; b++) {
-        or_bconv_centred(acc[b] + (size_t)ell * ln, P->mods + L, K, conv, P->mods, ell, n);
+#pragma omp parallel for schedule(dynamic)
+        for (int i = 0; i < ell; i++)
+            or_bconv_centred(acc[b] + (size_t)ell * ln, P->mods + L, K, conv + (size_t)i * ln, P->mods + i, 1, n);
         u64 *out = b == 0 ? out0 : out1;
         for (int i = 0; i < ell; i++)
             for (int k = 0; k < n; k++)
@@ -418,6 +426,7 @@ void or_rescale(const or_params *P, u64 *poly, int ell)
     size_t ln = (size_t)n;
     u64 qt = P->mods[ell - 1];
     const u64 *top = poly + (size_t)(ell - 1) * ln;
+#pragma omp parallel for schedule(dynamic)
     for (int i = 0; i < ell - 1; i++) {
         u64 qi = P->mods[i];
         u64 qt_inv = or_invmod(qt % qi, qi);
@@ -436,6 +445,7 @@ void or_rescale(const or_params *P, u64 *poly, int ell)
 void or_rns_polymul(const or_params *P, const u64 *a, const u64 *b, u64 *out, int nl, const int *mi)
 {
     size_t ln = (size_t)1 << P->log_n;
+#pragma omp parallel for schedule(dynamic)
     for (int l = 0; l < nl; l++)
         or_polymul(a + l * ln, b + l * ln, out + l * ln, P->log_n, P->mods[mi[l]], P->psis[mi[l]]);
 }
@@ -445,12 +455,14 @@ void or_rns_polymul(const or_params *P, const u64 *a, const u64 *b, u64 *out, in
 void or_rns_ntt_fwd(const or_params *P, u64 *a, int nl, const int *mi)
 {
     size_t ln = (size_t)1 << P->log_n;
+#pragma omp parallel for schedule(dynamic)
     for (int l = 0; l < nl; l++) or_ntt_fwd(a + l * ln, P->log_n, P->mods[mi[l]], P->psis[mi[l]]);
 }
 
 void or_rns_ntt_inv(const or_params *P, u64 *a, int nl, const int *mi)
 {
     size_t ln = (size_t)1 << P->log_n;
+#pragma omp parallel for schedule(dynamic)
     for (int l = 0; l < nl; l++) or_ntt_inv(a + l * ln, P->log_n, P->mods[mi[l]], P->psis[mi[l]]);
 }
 

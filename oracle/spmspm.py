@@ -101,14 +101,20 @@ def pack_values(data: np.ndarray, slots: int) -> list:
     return out
 
 
-def mask_scale(orc: Oracle) -> float:
-    """Reading R6: the mask is encoded at the scale of q_{L-2}."""
-    return float(orc.mods[orc.P.L - 2])
+def mask_scale(orc: Oracle, ell: int | None = None) -> float:
+    """Reading R6: for operands at level ell (default L) the mask is encoded at
+    the scale of q_{ell-2}, the prime the second rescale removes."""
+    ell = orc.P.L if ell is None else ell
+    return float(orc.mods[ell - 2])
 
 
-def result_scale(orc: Oracle) -> float:
-    """Scale of every accumulated product: Delta^2 / q_{L-1} (R6)."""
-    return orc.P.scale * orc.P.scale / orc.mods[orc.P.L - 1]
+def result_scale(orc: Oracle, ell: int | None = None, scale_a: float | None = None,
+                 scale_b: float | None = None) -> float:
+    """Scale of every accumulated product: scale_A * scale_B / q_{ell-1} (R6)."""
+    ell = orc.P.L if ell is None else ell
+    sa = orc.P.scale if scale_a is None else scale_a
+    sb = orc.P.scale if scale_b is None else scale_b
+    return sa * sb / orc.mods[ell - 1]
 
 
 @dataclass
@@ -121,9 +127,10 @@ class OpCounts:
 
 
 def make_mask(orc: Oracle, slot: int, level: int) -> Pt:
-    """makeMask(size^2, min_pos) of Alg. 2: one-hot plaintext at `slot`
-    (reading R8 for the encoding, R6 for the scale)."""
-    return orc.encode_onehot(1.0, slot, level, mask_scale(orc))
+    """makeMask(size^2, min_pos) of Alg. 2: one-hot plaintext at `slot` for a
+    product at `level` (= operand level - 1), scale q_{level-1} (readings R8,
+    R6)."""
+    return orc.encode_onehot(1.0, slot, level, float(orc.mods[level - 1]))
 
 
 def spmspm_ct_ct(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list,
@@ -132,8 +139,9 @@ def spmspm_ct_ct(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list
     """Alg. 1 + Alg. 2 over encrypted operands.
 
     A_csr = (indptr, indices) of A (rows x inner), B_csc = (indptr, indices) of
-    B (cols x inner column pointers).  A_cts / B_cts: packed chunks (R3) at
-    level L and scale Delta.  Returns the result chunks (R3) at level L-2.
+    B (cols x inner column pointers).  A_cts / B_cts: packed chunks (R3), all
+    at one level ell >= 3 (L for fresh ciphertexts).  Returns the result
+    chunks (R3) at level ell-2.
 
     mask_pt: optional one-hot mask at slot 0 (level L-1) to use in place of
     this oracle's own encoding; the mask for slot p is then the automorphism
@@ -144,7 +152,8 @@ def spmspm_ct_ct(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list
     if counts is None:
         counts = OpCounts()
     nres = max(1, -(-(rows * cols) // S))
-    result = [orc.zero_ct(P.L - 2, result_scale(orc)) for _ in range(nres)]
+    ell = A_cts[0].level
+    result = [orc.zero_ct(ell - 2, result_scale(orc, ell, A_cts[0].scale, B_cts[0].scale)) for _ in range(nres)]
     matches = alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols)
     if match_limit is not None:
         matches = matches[:match_limit]

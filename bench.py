@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); keyswitch HBM GB/s; p99"
-ALU_CLASSES = {"ntt_fwd", "ntt_inv", "modup_bconv", "moddown_bconv"}
+ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", "moddown_bconv"}
 
 
 def load_peaks():
@@ -190,6 +190,147 @@ class GpuMatmul:
 
 
 # ---------------------------------------------------------------------------
+# many products: batched call vs one call per product; serving loop
+# ---------------------------------------------------------------------------
+def _encrypt_case(sp, ctx, keys, case, level, scale, seed):
+    S = (1 << case.ring.log_n) // 2
+    Aip, Aix, Ad = to_csr(case.A)
+    Bip, Bix, Bd = to_csr(case.B.T)
+    Am = sp.sparse_meta(Aip, Aix, case.A.shape[0], case.A.shape[1])
+    Bm = sp.sparse_meta(Bip, Bix, case.B.shape[0], case.B.shape[1])
+
+    def enc(data, s0):
+        out = []
+        for c in range(max(1, -(-len(data) // S))):
+            z = np.zeros(S)
+            part = data[c * S:(c + 1) * S]
+            z[: len(part)] = part
+            pt = sp.spfhe_encode(ctx, z, level, scale)
+            out.append(sp.spfhe_encrypt(ctx, keys, pt, s0 + c))
+            sp.spfhe_pt_free(pt)
+        return out
+    return Am, enc(Ad, seed), Bm, enc(Bd, seed + 500), max(1, -(-(case.A.shape[0] * case.B.shape[1]) // S))
+
+
+def batch_vs_plain(stream, count, dims, seed=2):
+    """`count` products of the batch workload's recipe (d from `dims`,
+    sparsity U[0.70, 0.95], half Bernoulli / half 2:4) on its ring (N=2^16,
+    L=20, dnum=4): one spfhe_sparse_matmul_batch call against one
+    spfhe_sparse_matmul_ct_ct call per product.  Both produce identical bits."""
+    import torch
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    cases = synthetic.batch64_cases(seed=seed, count=count, dims=dims)
+    rec = cases[0].ring
+    ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    keys = sp.spfhe_keygen(ctx, 99)
+    prods = [_encrypt_case(sp, ctx, keys, c, rec.L, rec.scale, 10 * i) for i, c in enumerate(cases)]
+    reqs = [sp.matmul_req(keys, Am, a, Bm, b) for Am, a, Bm, b, _ in prods]
+    ncs = [p[4] for p in prods]
+
+    def plain():
+        outs, m = [], 0
+        for Am, a, Bm, b, nc in prods:
+            o, st = sp.spfhe_sparse_matmul_ct_ct(ctx, keys, Am, a, Bm, b, None, nc)
+            outs.append(o)
+            m += st["matches"]
+        return outs, m
+
+    def batched():
+        outs, st = sp.spfhe_sparse_matmul_batch(ctx, reqs, ncs)
+        return outs, sum(x["matches"] for x in st)
+
+    res = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        outs, m = fn()   # warm-up
+        for o in outs:
+            for h in o:
+                sp.spfhe_ct_free(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs, m = fn()
+        torch.cuda.synchronize()
+        res[name] = time.perf_counter() - t0
+        for o in outs:
+            for h in o:
+                sp.spfhe_ct_free(h)
+    for Am, a, Bm, b, nc in prods:
+        for h in a + b:
+            sp.spfhe_ct_free(h)
+    sp.spfhe_keys_free(keys)
+    sp.spfhe_ctx_destroy(ctx)
+    return {"workload": "%d products, d in %s, sparsity U[0.70,0.95] half 2:4, N=2^16, L=20, dnum=4 (scaled from "
+                        "64 products of d in {32..256})" % (count, list(dims)),
+            "matches": m, "plain_s": res["plain"], "batched_s": res["batched"],
+            "products_per_s_plain": count / res["plain"], "products_per_s_batched": count / res["batched"],
+            "speedup": res["plain"] / res["batched"]}
+
+
+def serve_run(stream, count, dims, rate, seed=4):
+    """Poisson stream of `count` requests (d from `dims`, sparsity U[0.5,0.95],
+    remaining levels U{10..30}, 4 key sets) on the serving ring (N=2^16, L=31,
+    dnum=4): the continuous-batching server against a plain loop that runs each
+    request alone in arrival order.  Latency = completion - arrival."""
+    import torch
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    reqs = synthetic.serving_stream(seed=seed, count=count, dims=dims, rate_per_s=rate)
+    rec = reqs[0].case.ring
+    ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    keysets = [sp.spfhe_keygen(ctx, 700 + k) for k in range(4)]
+    prods = [_encrypt_case(sp, ctx, keysets[r.key_set], r.case, r.level, rec.scale, 10 * i) for i, r in enumerate(reqs)]
+    torch.cuda.synchronize()
+    matches = 0
+    # plain: one request at a time, in arrival order, each alone
+    lat_plain = []
+    t0 = time.perf_counter()
+    for r, (Am, a, Bm, b, nc) in zip(reqs, prods):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        outs, st = sp.spfhe_sparse_matmul_ct_ct(ctx, keysets[r.key_set], Am, a, Bm, b, None, nc)
+        matches += st["matches"]
+        lat_plain.append((time.perf_counter() - t0) - r.arrival_s)
+        for h in outs:
+            sp.spfhe_ct_free(h)
+    plain_total = time.perf_counter() - t0
+    # served
+    srv = sp.spfhe_server_create(ctx, 64 << 30)
+    tickets = []
+    t0 = time.perf_counter()
+    for r, (Am, a, Bm, b, nc) in zip(reqs, prods):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        tickets.append((sp.spfhe_server_submit(srv, sp.matmul_req(keysets[r.key_set], Am, a, Bm, b)), nc))
+    got = []
+    for t, nc in tickets:
+        outs, st, lat = sp.spfhe_server_wait(srv, t, nc)
+        got.append((outs, lat))
+    served_total = time.perf_counter() - t0
+    sp.spfhe_server_destroy(srv)
+    lat_served = [lat / 1e3 for _, lat in got]
+    for outs, _ in got:
+        for h in outs:
+            sp.spfhe_ct_free(h)
+    for Am, a, Bm, b, nc in prods:
+        for h in a + b:
+            sp.spfhe_ct_free(h)
+    for k in keysets:
+        sp.spfhe_keys_free(k)
+    sp.spfhe_ctx_destroy(ctx)
+    q = lambda xs, p: float(np.percentile(np.array(xs) * 1e3, p))
+    return {"workload": "%d requests, Poisson %.1f/s, d in %s, sparsity U[0.5,0.95], levels U{10..30}, 4 key sets, "
+                        "N=2^16, L=31, dnum=4 (scaled from 2000 requests of d in {64..512})" % (count, rate, list(dims)),
+            "matches": matches,
+            "served": {"p50_ms": q(lat_served, 50), "p99_ms": q(lat_served, 99), "requests_per_s": count / served_total},
+            "plain": {"p50_ms": q(lat_plain, 50), "p99_ms": q(lat_plain, 99), "requests_per_s": count / plain_total},
+            "throughput_speedup": plain_total / served_total}
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
 class OracleSample:
@@ -289,6 +430,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_small_case(args):
+    """Profiler case that stays small (a few GB on the device): a 128x128
+    product at 99.5% sparsity on the workload's ring (N=2^16, L=24, dnum=3)
+    through the same Alg. 1 + Alg. 2 executor, 4 matches per batch, rotation
+    base 2 (15 rotation keys).  Every kernel of the timed step runs with the
+    same per-limb shapes; the key-switching buffers (4 x 93 limbs of 512 KiB)
+    exceed the 129 MB L2."""
+    import torch
+    from paper_2604_11659_gb300 import build as gbuild
+    from paper_2604_11659_gb300 import synthetic
+    gbuild.build()
+    os.environ["SPFHE_MATCH_BATCH"] = "4"
+    rng = np.random.default_rng(args.seed)
+    A = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
+    B = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
+    case = synthetic.MatmulCase("small", A, B, synthetic.ring_128x128())
+    g = GpuMatmul(case, 2, torch.cuda.current_stream().cuda_stream)
+    outs, st = g.step()
+    err = g.check(outs)
+    g.free(outs)
+    print("small case done: %d matches, max err %.2e" % (st["matches"], err))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,7 +464,15 @@ def main():
     ap.add_argument("--rot-base", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-products", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--small-case", action="store_true",
+                    help="profiler case: three relinearised products (tensor + key switch) at the workload's ring")
     args = ap.parse_args()
+    if args.small_case:
+        run_small_case(args)
+        return
     if args.workload == "16x16" and args.rot_base == 256:
         args.rot_base = 16
     if args.impl == "reference":
@@ -341,6 +513,7 @@ def main():
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.profiler.start()   # bounds ncu --profile-from-start off captures to the timed steps
         ev0.record()
         last = None
         for k in range(args.steps):
@@ -351,6 +524,7 @@ def main():
                 last = outs
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         barrier()
     clocks = clk.summary()
     ms_total = ev0.elapsed_time(ev1)
@@ -407,7 +581,10 @@ def main():
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tmulmod/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
-                "bytes_per_launch": dd["bytes"] / max(1, dd["launches"])}
+                "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
+                "work_per_launch": dd["work"] / max(1, dd["launches"]),
+                "algorithmic_bytes_per_launch": dd["bytes"] / max(1, dd["launches"]),
+                "hbm_gbs": dd["bytes"] / (dd["ms"] * 1e-3) / 1e9}
     else:
         achieved = dd["bytes"] / (dd["ms"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -430,6 +607,16 @@ def main():
             "keyswitch": {"polys": ks_calls, "gbs": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9,
                           "frac_of_hbm": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9 / hbm_peak},
             "kernels": kernels}
+    # batched vs plain, and serving, on scaled versions of the batch and
+    # serving workloads (their full sizes take hours per run at this speed)
+    sp.spfhe_keys_free(g.keys)
+    for hnd in g.A_cts + g.B_cts:
+        sp.spfhe_ct_free(hnd)
+    sp.spfhe_ctx_destroy(g.ctx)
+    if args.batch_products > 0:
+        line["batch"] = batch_vs_plain(stream, args.batch_products, (8, 16))
+    if args.serve_requests > 0:
+        line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(case, args.rot_base)
     if rank == 0:

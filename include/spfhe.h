@@ -278,6 +278,68 @@ spfhe_status spfhe_sparse_matmul_ct_pt(spfhe_ctx *ctx, const spfhe_keys *keys,
                                        spfhe_pt *const *B_pts, spfhe_ct **C_chunks, size_t n_c,
                                        spfhe_stats *stats);
 
+/* Rotation-plan base tuner (host only, no GPU work).  For the product A x B
+ * (Alg. 1's plan on the metadata) at ring degree 2^log_n with L, K, dnum,
+ * returns in *base the power of two b whose rotation plan needs the fewest
+ * key switches (distinct alignment rotations plus every final rotation; one
+ * key switch per nonzero base-b digit) among the bases whose rotation keys
+ * (every d*b^t < S, 1 <= d < b, each dnum*2*(L+K)*n words) fit
+ * key_budget_bytes; ties go to the smaller key set.  key_switches and
+ * key_bytes (may be NULL) receive that base's counts.  SPFHE_ENOMEM if no
+ * base fits. */
+spfhe_status spfhe_tune_rotation_base(uint32_t log_n, uint32_t L, uint32_t K, uint32_t dnum,
+                                      const spfhe_sparse_meta *A_csr, const spfhe_sparse_meta *B_csc,
+                                      uint64_t key_budget_bytes, uint32_t *base, uint64_t *key_switches,
+                                      uint64_t *key_bytes);
+
+/* ---- many products in one call, and the serving loop -------------------- */
+/* One encrypted product request (ct x ct, Alg. 1 + Alg. 2).  Fields as in
+ * spfhe_sparse_matmul_ct_ct; the operand chunks may sit at any level >= 3
+ * (all chunks of one request at the same level); results come back at that
+ * level - 2.  keys may differ between requests. */
+typedef struct {
+    const spfhe_keys *keys;
+    const spfhe_sparse_meta *A_csr;
+    spfhe_ct *const *A_chunks;
+    size_t n_a;
+    const spfhe_sparse_meta *B_csc;
+    spfhe_ct *const *B_chunks;
+    size_t n_b;
+    const spfhe_pt *mask0;   /* NULL: the library's own mask */
+} spfhe_matmul_req;
+
+/* n_req products in one call: their alignment rotations and matches are
+ * planned together and executed in shared batches (requests at the same
+ * level share launches; each relinearisation key stream serves every match
+ * of a batch that uses it).  C_chunks receives, request after request, each
+ * request's ceil(rows*cols / S) result chunks (n_c_total in all).  Every
+ * result is bit-identical to the one spfhe_sparse_matmul_ct_ct returns for the
+ * same request alone.  stats: NULL or n_req entries (launches counts the whole
+ * call). */
+spfhe_status spfhe_sparse_matmul_batch(spfhe_ctx *ctx, size_t n_req, const spfhe_matmul_req *reqs,
+                                       spfhe_ct **C_chunks, size_t n_c_total, spfhe_stats *stats);
+
+/* Continuous-batching server.  A worker thread owns the context until
+ * spfhe_server_destroy: do not use the context (or its handles) from other
+ * threads meanwhile, except through the server calls.  Between waves of
+ * work the worker admits submitted requests in arrival order while their
+ * result buffers fit hbm_budget_bytes (a request is always admitted when
+ * nothing else runs) and mixes their work into the running batches; results
+ * are bit-identical to running each request alone.  Operands and keys of a
+ * submitted request must stay alive until spfhe_server_wait returns for it;
+ * its metadata is copied at submission. */
+typedef struct spfhe_server spfhe_server;
+spfhe_status spfhe_server_create(spfhe_ctx *ctx, uint64_t hbm_budget_bytes, spfhe_server **out);
+spfhe_status spfhe_server_submit(spfhe_server *srv, const spfhe_matmul_req *req, uint64_t *ticket);
+/* Block until request `ticket` is done; hand its n_c result chunks to the
+ * caller; latency_ms = completion (its last kernel observed done) minus
+ * submission, host clock.  Errors of the request (EKEY, ELEVEL, ...) are
+ * returned here. */
+spfhe_status spfhe_server_wait(spfhe_server *srv, uint64_t ticket, spfhe_ct **C_chunks, size_t n_c,
+                               spfhe_stats *stats, double *latency_ms);
+/* Finish every submitted request, stop the worker, free unclaimed results. */
+spfhe_status spfhe_server_destroy(spfhe_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,7 +122,8 @@ spfhe_status spfhe_ctx_destroy(spfhe_ctx *ctx)
             c.rt->release();
             delete c.rt;
         }
-        if (c.mask0) dev_free(c, c.mask0);
+        for (auto &kv : c.masks) dev_free(c, kv.second);
+        c.masks.clear();
         cudaStreamSynchronize(c.stream);
         if (c.cos_tab) cudaFree(c.cos_tab);
         prof_destroy(c);

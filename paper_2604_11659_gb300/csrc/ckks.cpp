@@ -101,6 +101,12 @@ void rotate_step_batch(Ctx &ctx, int ell, const std::vector<const u64 *> &in, co
 void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u64 *> &in,
                   const std::vector<int> &r, u64 *out, uint64_t *ks)
 {
+    rotate_batch(ctx, std::vector<const Keys *>(in.size(), &keys), ell, in, r, out, ks);
+}
+
+void rotate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell, const std::vector<const u64 *> &in,
+                  const std::vector<int> &r, u64 *out, uint64_t *ks)
+{
     Runtime &rt = *ctx.rt;
     const int items = (int)in.size();
     if (!items) return;
@@ -110,7 +116,7 @@ void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u
     for (int i = 0; i < items; ++i) {
         plans[i] = rotation_plan(ctx, r[i]);
         T = std::max(T, plans[i].size());
-        for (int a : plans[i]) rotation_key(keys, a);   // EKEY before any launch
+        for (int a : plans[i]) rotation_key(*keys[i], a);   // EKEY before any launch
     }
     std::vector<const u64 *> cur(in.begin(), in.end());
     // items that need no rotation are copied straight to their output slot
@@ -131,13 +137,16 @@ void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u
         for (int i = 0; i < items; ++i)
             if (plans[i].size() > s) act.push_back(i);
         // group equal keys next to each other
-        std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return plans[a][s] < plans[b][s]; });
+        std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
+            const u64 *ka = rotation_key(*keys[a], plans[a][s]), *kb = rotation_key(*keys[b], plans[b][s]);
+            return ka < kb;
+        });
         std::vector<const u64 *> sin, skey;
         std::vector<int> sg;
         for (int i : act) {
             sin.push_back(cur[i]);
             sg.push_back(galois_element(ctx, plans[i][s]));
-            skey.push_back(rotation_key(keys, plans[i][s]));
+            skey.push_back(rotation_key(*keys[i], plans[i][s]));
         }
         u64 *dst = buf[s & 1];
         rotate_step_batch(ctx, ell, sin, sg, skey, dst);

@@ -42,6 +42,7 @@ struct DevTables {
     ModConst *mc = nullptr;          // [M]
     u64 *tw = nullptr, *twp = nullptr;     // [M][n]  psi^brv(k) and Shoup companions
     u64 *itw = nullptr, *itwp = nullptr;   // [M][n]  psi^-brv(k)
+    ulonglong2 *tw2 = nullptr, *itw2 = nullptr;   // [M][n] (twiddle, Shoup companion) pairs
     // ModUp basis conversion, one table per digit source set (indexed by the
     // digit's last limb + 1 = hi, 1..L): for source limb i of the digit
     // hat_inv[(hi-1)*alpha + i] (Shoup pair) and for every target modulus t
@@ -93,9 +94,9 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     DevTables dt;
-    // device-side mask plaintext (one-hot at slot 0, Montgomery form, [L-1][n]) of
-    // the library's own encoding, built on first use.
-    u64 *mask0 = nullptr;
+    // the library's own one-hot slot-0 masks (Montgomery form) per operand
+    // level ell: [ell-1][n] at scale q_{ell-2}, built on first use
+    std::map<int, u64 *> masks;
     uint64_t launches = 0;
     struct Runtime *rt = nullptr;    // workspace cache + metadata ring
     double *cos_tab = nullptr;       // cos(pi j / n), j < n (device), for one-hot encodings

@@ -238,8 +238,8 @@ template <int P> __device__ __forceinline__ int r16_tw(int j, int ls, int stage0
 // [0, 2q) first, w*y is taken in [0, 2q)), inverse values in [0, 2q); only
 // the last pass reduces to [0, q).  Needs 4q < 2^64.
 template <int P, int RND>
-__device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const u64 *__restrict__ w,
-                                              const u64 *__restrict__ wp, u64 q, int stage0, int btile)
+__device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
+                                              int stage0, int btile)
 {
     constexpr int Q = r16_q<P, RND>();
     const u64 q2 = 2 * q;
@@ -251,7 +251,8 @@ __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const u64 *__
             if (i & half) continue;
             const int j = r16_index<P, RND>(t, i);
             const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
-            const u64 W = __ldg(w + ti), Wp = __ldg(wp + ti);
+            const ulonglong2 wt = __ldg(w2 + ti);
+            const u64 W = wt.x, Wp = wt.y;
             const u64 x = csub(v[i], q2);
             const u64 y = mul_shoup_lazy(v[i + half], W, Wp, q);
             v[i] = x + y;
@@ -261,8 +262,8 @@ __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const u64 *__
 }
 
 template <int P, int RND>
-__device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const u64 *__restrict__ w,
-                                              const u64 *__restrict__ wp, u64 q, int stage0, int btile)
+__device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
+                                              int stage0, int btile)
 {
     constexpr int Q = r16_q<P, RND>();
     const u64 q2 = 2 * q;
@@ -274,7 +275,8 @@ __device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const u64 *__
             if (i & half) continue;
             const int j = r16_index<P, RND>(t, i);
             const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
-            const u64 W = __ldg(w + ti), Wp = __ldg(wp + ti);
+            const ulonglong2 wt = __ldg(w2 + ti);
+            const u64 W = wt.x, Wp = wt.y;
             const u64 x = v[i], y = v[i + half];
             v[i] = csub(x + y, q2);
             v[i + half] = mul_shoup_lazy(x - y + q2, W, Wp, q);
@@ -300,7 +302,7 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 
 template <int P>
 __global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const u64 *__restrict__ tw, const u64 *__restrict__ twp, int log_n)
+                                                 const ulonglong2 *__restrict__ tw2, int log_n)
 {
     __shared__ u64 sm[r16_smem_words_a<P>()];
     constexpr int TPC = kElems >> P;   // columns per CTA
@@ -309,21 +311,21 @@ __global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__re
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
-    const u64 *w = tw + (size_t)mi * n, *wp = twp + (size_t)mi * n;
+    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int lg_ncols = log_n - P;
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
-    r16_fwd_round<P, 0>(v, t, w, wp, q, 0, 0);
+    r16_fwd_round<P, 0>(v, t, w2, q, 0, 0);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1>(v, t, w, wp, q, 0, 0);
+        r16_fwd_round<P, 1>(v, t, w2, q, 0, 0);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2>(v, t, w, wp, q, 0, 0);
+        r16_fwd_round<P, 2>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__re
 
 template <int P>
 __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const u64 *__restrict__ tw, const u64 *__restrict__ twp, int log_n,
+                                                 const ulonglong2 *__restrict__ tw2, int log_n,
                                                  int PA)
 {
     __shared__ u64 sm[r16_smem_words_b<P>()];
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
-    const u64 *w = tw + (size_t)mi * n, *wp = twp + (size_t)mi * n;
+    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
     const size_t e0 = (size_t)blockIdx.x * kElems;
     const int btile = (int)(e0 >> P) + tile;
@@ -358,14 +360,14 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = tp[r16_index<P, 0>(t, i)];
-    r16_fwd_round<P, 0>(v, t, w, wp, q, PA, btile);
+    r16_fwd_round<P, 0>(v, t, w2, q, PA, btile);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1>(v, t, w, wp, q, PA, btile);
+        r16_fwd_round<P, 1>(v, t, w2, q, PA, btile);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2>(v, t, w, wp, q, PA, btile);
+        r16_fwd_round<P, 2>(v, t, w2, q, PA, btile);
     }
     // the last round holds 16 contiguous elements per thread: stage through
     // shared memory so the global stores are coalesced
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
 
 template <int P>
 __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const u64 *__restrict__ itw, const u64 *__restrict__ itwp,
+                                                 const ulonglong2 *__restrict__ tw2,
                                                  int log_n, int PA)
 {
     __shared__ u64 sm[r16_smem_words_b<P>()];
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
-    const u64 *w = itw + (size_t)mi * n, *wp = itwp + (size_t)mi * n;
+    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
     const size_t e0 = (size_t)blockIdx.x * kElems;
     const int btile = (int)(e0 >> P) + tile;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
-    r16_inv_round<P, R - 1>(v, t, w, wp, q, PA, btile);
+    r16_inv_round<P, R - 1>(v, t, w2, q, PA, btile);
     if constexpr (R > 2) {
         __syncthreads();
 #pragma unroll
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2>(v, t, w, wp, q, PA, btile);
+        r16_inv_round<P, R - 2>(v, t, w2, q, PA, btile);
     }
     if constexpr (R > 1) {
         __syncthreads();
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0>(v, t, w, wp, q, PA, btile);
+        r16_inv_round<P, 0>(v, t, w2, q, PA, btile);
     }
     u64 *tp = p + e0 + ((size_t)tile << P);
 #pragma unroll
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
 
 template <int P>
 __global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const u64 *__restrict__ itw, const u64 *__restrict__ itwp,
+                                                 const ulonglong2 *__restrict__ tw2,
                                                  int log_n)
 {
     __shared__ u64 sm[r16_smem_words_a<P>()];
@@ -443,21 +445,21 @@ __global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__re
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
     const u64 q = m.q;
-    const u64 *w = itw + (size_t)mi * n, *wp = itwp + (size_t)mi * n;
+    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int lg_ncols = log_n - P;
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol];
-    r16_inv_round<P, R - 1>(v, t, w, wp, q, 0, 0);
+    r16_inv_round<P, R - 1>(v, t, w2, q, 0, 0);
     if constexpr (R > 2) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, R - 1>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2>(v, t, w, wp, q, 0, 0);
+        r16_inv_round<P, R - 2>(v, t, w2, q, 0, 0);
         __syncthreads();
     }
     if constexpr (R > 1) {
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0>(v, t, w, wp, q, 0, 0);
+        r16_inv_round<P, 0>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -476,19 +478,19 @@ __global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__re
 template <int P> struct R16Launch {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
-        k_fwd16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw, c.dt.twp, c.log_n);
+        k_fwd16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
     {
-        k_fwd16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw, c.dt.twp, c.log_n, PA);
+        k_fwd16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA);
     }
     static void inv_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
-        k_inv16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw, c.dt.itwp, c.log_n);
+        k_inv16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n);
     }
     static void inv_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
     {
-        k_inv16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw, c.dt.itwp, c.log_n, PA);
+        k_inv16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n, PA);
     }
 };
 

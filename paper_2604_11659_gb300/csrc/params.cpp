@@ -164,6 +164,13 @@ void upload_tables(Ctx &ctx)
     t.twp = upload(twp);
     t.itw = upload(itw);
     t.itwp = upload(itwp);
+    std::vector<ulonglong2> tw2((size_t)M * n), itw2((size_t)M * n);
+    for (size_t k = 0; k < tw2.size(); ++k) {
+        tw2[k] = make_ulonglong2(tw[k], twp[k]);
+        itw2[k] = make_ulonglong2(itw[k], itwp[k]);
+    }
+    t.tw2 = upload(tw2);
+    t.itw2 = upload(itw2);
 
     // ModUp: one table per digit source set [lo, hi)
     std::vector<u64> hinv((size_t)L * A), hinvp((size_t)L * A), hmont((size_t)L * A * M);
@@ -265,6 +272,8 @@ void free_tables(Ctx &ctx)
         if (p) cudaFree(p);
     if (t.mc) cudaFree(t.mc);
     if (t.inv_q) cudaFree(t.inv_q);
+    if (t.tw2) cudaFree(t.tw2);
+    if (t.itw2) cudaFree(t.itw2);
     t = DevTables{};
 }
 

@@ -64,6 +64,9 @@ void rotate_step_batch(Ctx &ctx, int ell, const std::vector<const u64 *> &in, co
 // results in out [items][2][ell][n].  counts the key switches in *ks.
 void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u64 *> &in,
                   const std::vector<int> &r, u64 *out, uint64_t *ks);
+// the same with a key set per item
+void rotate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell, const std::vector<const u64 *> &in,
+                  const std::vector<int> &r, u64 *out, uint64_t *ks);
 
 std::vector<int> rotation_plan(const Ctx &ctx, long long r);
 int galois_element(const Ctx &ctx, int r);   // 5^r mod 2n

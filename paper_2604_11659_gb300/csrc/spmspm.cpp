@@ -22,7 +22,7 @@
 #include <map>
 #include <tuple>
 
-#include "runtime.h"
+#include "engine.h"
 
 namespace spfhe {
 
@@ -89,22 +89,6 @@ std::vector<MatchRec> plan_alg1(const spfhe_sparse_meta &A, const spfhe_sparse_m
     return out;
 }
 
-static int env_int(const char *name, int dflt)
-{
-    const char *v = std::getenv(name);
-    if (!v || !*v) return dflt;
-    const int x = std::atoi(v);
-    return x > 0 ? x : dflt;
-}
-
-// Matches per batch: bounded by a per-item memory estimate so the working
-// set stays within a few tens of GB at any ring size.
-static int match_batch(const Ctx &ctx)
-{
-    const int dflt = ctx.n >= (1 << 15) ? 32 : 64;
-    return std::max(1, std::min(env_int("SPFHE_MATCH_BATCH", dflt), 1024));
-}
-
 static void check_chunks(Ct *const *ch, size_t n, int level, const char *what)
 {
     for (size_t c = 0; c < n; ++c) {
@@ -115,29 +99,33 @@ static void check_chunks(Ct *const *ch, size_t n, int level, const char *what)
     }
 }
 
-static size_t chunks_for(long long count, int S) { return (size_t)std::max(1LL, (count + S - 1) / S); }
-
-static const u64 *mask_montgomery(Ctx &ctx, const Pt *mask0)
+void fill_job(Job &job, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
+              const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, size_t nC)
 {
-    const int ell = ctx.L - 1;
-    const size_t words = (size_t)ell * ctx.n;
-    std::vector<int> mi(ell);
-    for (int i = 0; i < ell; ++i) mi[i] = i;
-    if (mask0) {
-        if (mask0->level != ell) throw Error(SPFHE_ELEVEL, "mask must be at level L-1");
-        u64 *m = ctx.rt->workspace(WS_MASK, words);
-        copy_words(ctx, m, mask0->d, words);
-        to_montgomery(ctx, m, ell, mi.data(), 1);
-        return m;
-    }
-    if (!ctx.mask0) {
-        ctx.mask0 = static_cast<u64 *>(dev_alloc(ctx, words * sizeof(u64)));
-        const double one = 1.0;
-        const double *d_one = static_cast<const double *>(ctx.rt->upload(&one, sizeof(double)));
-        encode_onehot0(ctx, d_one, 1, ell, (double)ctx.mods[ctx.L - 2], ctx.mask0);
-        to_montgomery(ctx, ctx.mask0, ell, mi.data(), 1);
-    }
-    return ctx.mask0;
+    job.keys = &keys;
+    job.A = A;
+    job.B = B;
+    job.aip.assign(A.indptr, A.indptr + A.rows + 1);
+    if (A.nnz > 0) job.aix.assign(A.indices, A.indices + A.nnz);
+    job.bip.assign(B.indptr, B.indptr + B.cols + 1);
+    if (B.nnz > 0) job.bix.assign(B.indices, B.indices + B.nnz);
+    job.Ach.assign(Ach, Ach + nA);
+    job.Bch.assign(Bch, Bch + nB);
+    job.mask0 = mask0;
+    job.n_c = nC;
+}
+
+void release_job(Ctx &ctx, Job &job, bool free_results)
+{
+    if (job.own_mask) dev_free(ctx, job.own_mask);
+    job.own_mask = nullptr;
+    if (free_results)
+        for (Ct *&c : job.C)
+            if (c) {
+                dev_free(ctx, c->d);
+                delete c;
+                c = nullptr;
+            }
 }
 
 struct Stats {
@@ -172,156 +160,26 @@ void spmspm_ct_ct(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
 {
     const uint64_t launches0 = ctx.launches;
     validate_pair(A, B);
-    const int S = ctx.S, L = ctx.L;
-    const size_t n = ctx.n;
-    if (L < 3) throw Error(SPFHE_ELEVEL, "ct x ct needs L >= 3");
-    if (nA != chunks_for(A.nnz, S) || nB != chunks_for(B.nnz, S))
-        throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
-    if (nC != chunks_for((long long)A.rows * B.cols, S)) throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
-    check_chunks(Ach, nA, L, "A");
-    check_chunks(Bch, nB, L, "B");
-    if (std::fabs(Ach[0]->scale - Bch[0]->scale) > 1e-9 * Ach[0]->scale) throw Error(SPFHE_ESCALE, "A and B scales differ");
     for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
-
-    const std::vector<MatchRec> matches = plan_alg1(A, B);
-    const double rscale = Ach[0]->scale * Bch[0]->scale / (double)ctx.mods[L - 1];
-    const int ellC = L - 2;
-    Stats st;
+    Job job;
+    fill_job(job, keys, A, Ach, nA, B, Bch, nB, mask0, nC);
+    Engine eng(ctx);
     try {
-        for (size_t c = 0; c < nC; ++c) {
-            C[c] = ct_new(ctx, ellC, rscale);
-            SPFHE_CHECK_CUDA(cudaMemsetAsync(C[c]->d, 0, 2ull * ellC * n * sizeof(u64), ctx.stream));
-        }
-        if (!matches.empty()) {
-            if (!keys.relin) throw Error(SPFHE_EKEY, "no relinearisation key");
-            Runtime &rt = *ctx.rt;
-            const u64 *mask = mask_montgomery(ctx, mask0);
-            // alignment sources: (operand, chunk, amount) -> rotated-operand index
-            struct M2 {
-                int src_a, src_b;   // >= 0: rotated-operand index; < 0: -(chunk + 1) of the plain operand
-                int min_slot, rf, rc;
-            };
-            std::map<std::tuple<int, int, int>, int> rot_index;
-            std::vector<std::tuple<int, int, int>> rot_list;
-            std::vector<M2> ms(matches.size());
-            auto rot_of = [&](int op, int chunk, int amt) {
-                auto key = std::make_tuple(op, chunk, amt);
-                auto it = rot_index.find(key);
-                if (it != rot_index.end()) return it->second;
-                const int id = (int)rot_list.size();
-                rot_index[key] = id;
-                rot_list.push_back(key);
-                return id;
-            };
-            for (size_t x = 0; x < matches.size(); ++x) {
-                const MatchRec &mt = matches[x];
-                const int ca = mt.a_pos / S, sa = mt.a_pos % S, cb = mt.b_pos / S, sb = mt.b_pos % S;
-                M2 m2;
-                m2.src_a = -(ca + 1);
-                m2.src_b = -(cb + 1);
-                m2.min_slot = sa;
-                if (sa < sb) {
-                    m2.src_b = rot_of(1, cb, sb - sa);
-                } else if (sb < sa) {
-                    m2.src_a = rot_of(0, ca, sa - sb);
-                    m2.min_slot = sb;
-                }
-                const long long t = (long long)mt.i * B.cols + mt.j;
-                m2.rc = (int)(t / S);
-                m2.rf = (int)(((m2.min_slot - t % S) % S + S) % S);
-                ms[x] = m2;
-            }
-            // every key the run needs exists before the first launch
-            for (auto &r : rot_list)
-                for (int a : rotation_plan(ctx, std::get<2>(r))) rotation_key(keys, a);
-            for (auto &m2 : ms)
-                for (int a : rotation_plan(ctx, m2.rf)) rotation_key(keys, a);
-
-            const int Bm = match_batch(ctx);
-            const int G = Bm;
-            const long long csL = 2LL * L * n;
-            const int nwaves = std::max<int>(1, (int)((rot_list.size() + G - 1) / G));
-            std::vector<std::vector<int>> wave_matches(nwaves);
-            for (size_t x = 0; x < ms.size(); ++x) {
-                int w = 0;
-                if (ms[x].src_a >= 0) w = ms[x].src_a / G;
-                if (ms[x].src_b >= 0) w = ms[x].src_b / G;
-                wave_matches[w].push_back((int)x);
-            }
-            u64 *align = rt.workspace(WS_ALIGN, (size_t)std::max<size_t>(1, std::min<size_t>(G, rot_list.size())) * csL);
-            std::vector<int> mask_g_cache(S, 0);
-            for (int w = 0; w < nwaves; ++w) {
-                const int r0 = w * G, r1 = std::min<int>((int)rot_list.size(), r0 + G);
-                if (r1 > r0) {
-                    std::vector<const u64 *> rin;
-                    std::vector<int> ramt;
-                    for (int r = r0; r < r1; ++r) {
-                        const int op = std::get<0>(rot_list[r]), chunk = std::get<1>(rot_list[r]);
-                        rin.push_back((op == 0 ? Ach[chunk] : Bch[chunk])->d);
-                        ramt.push_back(std::get<2>(rot_list[r]));
-                    }
-                    rotate_batch(ctx, keys, L, rin, ramt, align, &st.ks_align);
-                }
-                auto operand = [&](int src, Ct *const *plain) -> const u64 * {
-                    if (src < 0) return plain[-src - 1]->d;
-                    return align + (long long)(src - r0) * csL;
-                };
-                const std::vector<int> &wm = wave_matches[w];
-                for (size_t b0 = 0; b0 < wm.size(); b0 += Bm) {
-                    const int m = (int)std::min<size_t>(Bm, wm.size() - b0);
-                    std::vector<const u64 *> pa(m), pb(m), d2(m), dbase(m), x1(m), x2(m), mk(m);
-                    std::vector<int> gm(m), rf(m), rc(m);
-                    u64 *D = rt.workspace(WS_TENSOR, (size_t)m * 3 * L * n);
-                    u64 *X = rt.workspace(WS_RELIN_OUT, (size_t)m * csL);
-                    u64 *Y = rt.workspace(WS_LEVEL1, (size_t)m * 2 * (L - 1) * n);
-                    u64 *Z = rt.workspace(WS_LEVEL2, (size_t)m * 2 * (L - 2) * n);
-                    u64 *T = rt.workspace(WS_RS_TMP, (size_t)m * 2 * L * n);
-                    for (int i = 0; i < m; ++i) {
-                        const M2 &m2 = ms[wm[b0 + i]];
-                        pa[i] = operand(m2.src_a, Ach);
-                        pb[i] = operand(m2.src_b, Bch);
-                        dbase[i] = D + (size_t)i * 3 * L * n;
-                        d2[i] = dbase[i] + 2 * L * n;
-                        x1[i] = X + i * csL;
-                        x2[i] = Y + (size_t)i * 2 * (L - 1) * n;
-                        mk[i] = mask;
-                        // the mask for slot p is sigma_h of the slot-0 mask, h = 5^-p
-                        gm[i] = galois_element(ctx, -m2.min_slot);
-                        rf[i] = m2.rf;
-                        rc[i] = m2.rc;
-                    }
-                    tensor(ctx, m, L, rt.upload_vec(pa), rt.upload_vec(pb), D);
-                    std::vector<KeyGroup> groups;
-                    const int gsz = 8;
-                    for (int i = 0; i < m; i += gsz) groups.push_back(KeyGroup{keys.relin, i, std::min(gsz, m - i)});
-                    keyswitch_batch(ctx, m, L, rt.upload_vec(d2), groups, rt.upload_vec(dbase), nullptr, true, X, csL);
-                    st.ks_relin += m;
-                    rescale(ctx, m, L, rt.upload_vec(x1), T, Y, 2LL * (L - 1) * n);
-                    mul_plain_perm(ctx, m, L - 1, Y, 2LL * (L - 1) * n, rt.upload_vec(mk), rt.upload_vec(gm));
-                    // Relinearize after a plaintext product has nothing to switch
-                    rescale(ctx, m, L - 1, rt.upload_vec(x2), T, Z, 2LL * (L - 2) * n);
-                    st.rescales += 2ull * m;
-                    rotate_and_accumulate(ctx, keys, L - 2, Z, m, rf, rc, C, nC, st);
-                    st.matches += m;
-                }
-            }
-        }
+        eng.add(&job);
+        eng.run_all();
         SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
     } catch (...) {
-        for (size_t c = 0; c < nC; ++c)
-            if (C[c]) {
-                dev_free(ctx, C[c]->d);
-                delete C[c];
-                C[c] = nullptr;
-            }
+        release_job(ctx, job, true);
         throw;
     }
+    for (size_t c = 0; c < nC; ++c) C[c] = job.C[c];
+    release_job(ctx, job, false);
     if (out_stats) {
-        out_stats->matches = st.matches;
-        out_stats->ks_relin = st.ks_relin;
-        out_stats->ks_align = st.ks_align;
-        out_stats->ks_final = st.ks_final;
-        out_stats->rescales = st.rescales;
+        out_stats->matches = job.st_matches;
+        out_stats->ks_relin = job.st_relin;
+        out_stats->ks_align = job.st_align;
+        out_stats->ks_final = job.st_final;
+        out_stats->rescales = job.st_rescales;
         out_stats->launches = ctx.launches - launches0;
     }
 }
@@ -362,7 +220,7 @@ void spmspm_ct_pt(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
                 const long long t = (long long)mt.i * B.cols + mt.j;
                 for (int a : rotation_plan(ctx, ((mt.a_pos % S - t % S) % S + S) % S)) rotation_key(keys, a);
             }
-            const int Bm = match_batch(ctx);
+            const int Bm = match_batch_size(ctx);
             const long long csL = 2LL * L * n;
             const long long plimb = (long long)L * n;
             for (size_t b0 = 0; b0 < order.size(); b0 += Bm) {

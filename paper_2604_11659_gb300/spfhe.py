@@ -104,6 +104,26 @@ _SIGS = [
                                                  ctypes.POINTER(Stats)]),
 ]
 
+class MatmulReq(ctypes.Structure):
+    _fields_ = [("keys", handle), ("A_csr", ctypes.POINTER(SparseMeta)), ("A_chunks", ctypes.POINTER(handle)),
+                ("n_a", ctypes.c_size_t), ("B_csc", ctypes.POINTER(SparseMeta)), ("B_chunks", ctypes.POINTER(handle)),
+                ("n_b", ctypes.c_size_t), ("mask0", handle)]
+
+
+_SIGS += [
+    ("spfhe_sparse_matmul_batch", ctypes.c_int, [handle, ctypes.c_size_t, ctypes.POINTER(MatmulReq),
+                                                 ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
+    ("spfhe_server_create", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
+    ("spfhe_server_submit", ctypes.c_int, [handle, ctypes.POINTER(MatmulReq), ctypes.POINTER(ctypes.c_uint64)]),
+    ("spfhe_server_wait", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle), ctypes.c_size_t,
+                                         ctypes.POINTER(Stats), c_dblp]),
+    ("spfhe_server_destroy", ctypes.c_int, [handle]),
+    ("spfhe_tune_rotation_base", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                ctypes.POINTER(SparseMeta), ctypes.POINTER(SparseMeta),
+                                                ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
+                                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+]
+
 EXPORTED = [s[0] for s in _SIGS]
 
 
@@ -388,6 +408,65 @@ def spfhe_sparse_matmul_ct_ct(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta,
                                            ctypes.byref(B), _handles(B_chunks), len(B_chunks), mask0, outs, n_c,
                                            ctypes.byref(st)))
     return [handle(outs[i]) for i in range(n_c)], st.as_dict()
+
+
+def matmul_req(keys, A: SparseMeta, A_chunks, B: SparseMeta, B_chunks, mask0=None) -> MatmulReq:
+    a = _handles(A_chunks)
+    b = _handles(B_chunks)
+    r = MatmulReq(keys, ctypes.pointer(A), a, len(A_chunks), ctypes.pointer(B), b, len(B_chunks), mask0)
+    r._keep = (A, B, a, b)
+    return r
+
+
+def n_result_chunks(A: SparseMeta, B: SparseMeta, slots: int) -> int:
+    return max(1, -(-(A.rows * B.cols) // slots))
+
+
+def spfhe_sparse_matmul_batch(ctx, reqs, n_c_per_req):
+    arr = (MatmulReq * max(1, len(reqs)))(*reqs)
+    total = sum(n_c_per_req)
+    outs = (handle * max(1, total))()
+    st = (Stats * max(1, len(reqs)))()
+    _check(lib().spfhe_sparse_matmul_batch(ctx, len(reqs), arr, outs, total, st))
+    res, o = [], 0
+    for k in n_c_per_req:
+        res.append([handle(outs[o + i]) for i in range(k)])
+        o += k
+    return res, [st[i].as_dict() for i in range(len(reqs))]
+
+
+def spfhe_server_create(ctx, hbm_budget_bytes: int):
+    out = handle()
+    _check(lib().spfhe_server_create(ctx, int(hbm_budget_bytes), ctypes.byref(out)))
+    return out
+
+
+def spfhe_server_submit(srv, req: MatmulReq) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().spfhe_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def spfhe_server_wait(srv, ticket: int, n_c: int):
+    outs = (handle * n_c)()
+    st = Stats()
+    lat = ctypes.c_double()
+    _check(lib().spfhe_server_wait(srv, ticket, outs, n_c, ctypes.byref(st), ctypes.byref(lat)))
+    return [handle(outs[i]) for i in range(n_c)], st.as_dict(), lat.value
+
+
+def spfhe_tune_rotation_base(log_n: int, L: int, K: int, dnum: int, A: SparseMeta, B: SparseMeta,
+                             key_budget_bytes: int):
+    b = ctypes.c_uint32()
+    ks = ctypes.c_uint64()
+    kb = ctypes.c_uint64()
+    _check(lib().spfhe_tune_rotation_base(log_n, L, K, dnum, ctypes.byref(A), ctypes.byref(B), int(key_budget_bytes),
+                                          ctypes.byref(b), ctypes.byref(ks), ctypes.byref(kb)))
+    return int(b.value), int(ks.value), int(kb.value)
+
+
+def spfhe_server_destroy(srv):
+    _check(lib().spfhe_server_destroy(srv))
 
 
 def spfhe_sparse_matmul_ct_pt(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta, B_values, B_pts, n_c: int):

@@ -150,13 +150,19 @@ def case_dense_layer(seed: int = 3, plain_weights: bool = False) -> MatmulCase:
     return MatmulCase("dense_layer_64x784x128", A, W, ring_dense_layer(), B_plain=plain_weights)
 
 
-def batch64_cases(seed: int = 2, count: int = 64) -> list:
-    """`count` independent square products: d in {32, 64, 128, 256}, sparsity
-    uniform in [0.70, 0.95], half i.i.d. Bernoulli, half 2:4 structured."""
+def ring_serving() -> RingRecipe:
+    """N=2^16, L=31 (q_0 60-bit + 30 x 45-bit), dnum=4, scale 2^45."""
+    return RingRecipe(log_n=16, q_bits=[60] + [45] * 30, dnum=4, scale_bits=45, k_stated=0, rot_base=16)
+
+
+def batch64_cases(seed: int = 2, count: int = 64, dims=(32, 64, 128, 256)) -> list:
+    """`count` independent square products: d drawn from `dims` (the batch
+    workload uses {32, 64, 128, 256}), sparsity uniform in [0.70, 0.95], half
+    i.i.d. Bernoulli, half 2:4 structured."""
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
-        d = int(rng.choice([32, 64, 128, 256]))
+        d = int(rng.choice(list(dims)))
         s = float(rng.uniform(0.70, 0.95))
         if b % 2 == 0:
             A = bernoulli_sparse(rng, d, d, s)
@@ -181,3 +187,34 @@ def tiny_case(seed: int, d: int, sparsity: float, log_n: int = 6, L: int = 4, dn
     A = rescale_rows_to_unit_output(A, B)
     return MatmulCase("tiny_%dx%dx%d" % (rows, inner, cols), A, B,
                       ring_tiny(log_n, L, dnum, rot_base))
+
+
+@dataclass
+class ServeRequest:
+    case: MatmulCase
+    level: int          # operand level (limbs) of the request's ciphertexts
+    key_set: int
+    arrival_s: float
+
+
+def serving_stream(seed: int = 4, count: int = 2000, dims=(64, 128, 256, 512), rate_per_s: float = 1.0,
+                   key_sets: int = 4, levels=(10, 30)) -> list:
+    """Poisson arrivals (exponential gaps, `rate_per_s`) of square products:
+    d from `dims`, sparsity uniform in [0.50, 0.95] (i.i.d.), remaining levels
+    uniform in `levels` (operand level = remaining + 1 limbs), key set uniform
+    over `key_sets`."""
+    rng = np.random.default_rng(seed)
+    ring = ring_serving()
+    t = 0.0
+    out = []
+    for r in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        d = int(rng.choice(list(dims)))
+        s = float(rng.uniform(0.50, 0.95))
+        A = bernoulli_sparse(rng, d, d, s)
+        B = bernoulli_sparse(rng, d, d, s)
+        A = rescale_rows_to_unit_output(A, B)
+        lvl = int(rng.integers(levels[0], levels[1] + 1)) + 1
+        out.append(ServeRequest(MatmulCase("req%d_d%d" % (r, d), A, B, ring, meta={"d": d, "sparsity": s}),
+                                lvl, int(rng.integers(0, key_sets)), t))
+    return out

@@ -106,6 +106,8 @@ def lib():
         L.or_rns_polymul.argtypes = [pp, u64p, u64p, u64p, ctypes.c_int, ip]
         L.or_rns_ntt_fwd.argtypes = [pp, u64p, ctypes.c_int, ip]
         L.or_rns_ntt_inv.argtypes = [pp, u64p, ctypes.c_int, ip]
+        L.or_threads.argtypes = [ctypes.c_int]
+        L.or_threads.restype = ctypes.c_int
         L.or_mulmod_vec.argtypes = [u64p, u64p, u64p, ctypes.c_size_t, u64]
         L.or_mulmod_scalar.argtypes = [u64p, u64, u64p, ctypes.c_size_t, u64]
         _lib = L
@@ -125,6 +127,11 @@ def _ip(a: np.ndarray):
 # ---------------------------------------------------------------------------
 # small wrappers over the C primitives
 # ---------------------------------------------------------------------------
+def threads(n: int = 0) -> int:
+    """Set (n > 0) and return the number of OpenMP threads of the limb loops."""
+    return int(lib().or_threads(n))
+
+
 def is_prime(x: int) -> bool:
     return bool(lib().or_is_prime(x))
 
@@ -428,7 +435,7 @@ class Oracle:
         self.n = params.n
         self.mods = params.mods
         if nthreads is not None:
-            os.environ["OMP_NUM_THREADS"] = str(nthreads)
+            threads(nthreads)
 
     # -- helpers -----------------------------------------------------------
     def _mi(self, ell: int) -> np.ndarray:

@@ -21,6 +21,7 @@
  * every limb is computed by the same code either way.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -464,6 +465,14 @@ void or_rns_ntt_inv(const or_params *P, u64 *a, int nl, const int *mi)
     size_t ln = (size_t)1 << P->log_n;
 #pragma omp parallel for schedule(dynamic)
     for (int l = 0; l < nl; l++) or_ntt_inv(a + l * ln, P->log_n, P->mods[mi[l]], P->psis[mi[l]]);
+}
+
+/* OpenMP threads used by the limb loops (0 = leave unchanged); returns the
+ * current maximum. */
+int or_threads(int nthreads)
+{
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
 }
 
 /* a*b mod q for numpy callers (vectorised over cnt elements) */

@@ -150,6 +150,15 @@ spfhe_status spfhe_sync(spfhe_ctx *ctx)
 
 uint64_t spfhe_launch_count(const spfhe_ctx *ctx) { return ctx ? ctx->c.launches : 0; }
 
+spfhe_status spfhe_ctx_set_match_batch(spfhe_ctx *ctx, uint32_t matches)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        need(matches <= 1024, "batch size out of range");
+        ctx->c.match_batch = (int)matches;
+    });
+}
+
 spfhe_status spfhe_prof_enable(spfhe_ctx *ctx, int enable)
 {
     return guard([&] {

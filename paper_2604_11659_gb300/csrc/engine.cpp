@@ -18,6 +18,7 @@ static int env_int(const char *name, int dflt)
 
 int match_batch_size(const Ctx &ctx)
 {
+    if (ctx.match_batch > 0) return ctx.match_batch;
     const int dflt = ctx.n >= (1 << 15) ? 32 : 64;
     return std::max(1, std::min(env_int("SPFHE_MATCH_BATCH", dflt), 1024));
 }

@@ -102,6 +102,7 @@ struct Ctx {
     double *cos_tab = nullptr;       // cos(pi j / n), j < n (device), for one-hot encodings
     Prof prof;
     int in_keyswitch = 0;            // NTT launches inside key switching are classed separately
+    int match_batch = 0;             // matches per batch (0: default for the ring size)
 };
 
 struct Keys {

@@ -61,6 +61,7 @@ _SIGS = [
     ("spfhe_ctx_moduli", ctypes.c_int, [handle, c_u64p, c_u64p]),
     ("spfhe_sync", ctypes.c_int, [handle]),
     ("spfhe_launch_count", ctypes.c_uint64, [handle]),
+    ("spfhe_ctx_set_match_batch", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_prof_enable", ctypes.c_int, [handle, ctypes.c_int]),
     ("spfhe_prof_read", ctypes.c_int, [handle, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), c_dblp, c_dblp, c_dblp]),
     ("spfhe_prof_classes", ctypes.c_int, []),
@@ -201,6 +202,10 @@ def spfhe_ctx_moduli(ctx, count: int):
 
 def spfhe_sync(ctx):
     _check(lib().spfhe_sync(ctx))
+
+
+def spfhe_ctx_set_match_batch(ctx, matches: int):
+    _check(lib().spfhe_ctx_set_match_batch(ctx, int(matches)))
 
 
 def spfhe_launch_count(ctx) -> int:

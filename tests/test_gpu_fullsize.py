@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_bench_ring_bit_exact_few_matches():
-    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    ckks.threads(os.cpu_count() or 1)
     recipe = synthetic.ring_128x128()
     A = np.zeros((128, 128))
     B = np.zeros((128, 128))

@@ -125,10 +125,45 @@ def to_csr(M):
     return np.array(ip, np.int32), np.array(ix, np.int32), np.array(d, np.float64)
 
 
+NTT_CHUNKS = (0, 64, 128, 256, 512)
+
+
+def tune_ntt(sp, ctx, rec, chunk):
+    """chunk >= 0: set it (default split and kernel variant); -1: for every
+    kernel variant and split of the two-pass NTT into pass A / pass B stages,
+    time the launch-chunk candidates on one match batch of key switches at the
+    top level, and keep the fastest.  Returns ((variant, split, chunk),
+    timings keyed "variant/split/chunk")."""
+    if chunk >= 0:
+        sp.spfhe_ctx_set_ntt_chunk(ctx, chunk)
+        return (0, 0, chunk), None
+    items = 32 if rec.log_n >= 15 else 64
+    splits = [pa for pa in range(6, 10) if 6 <= rec.log_n - pa <= 9] if rec.log_n >= 12 else [0]
+    best, timings = None, {}
+    for var in (0, 1, 2):
+        sp.spfhe_ctx_set_ntt_variant(ctx, var)
+        for pa in splits:
+            sp.spfhe_ctx_set_ntt_split(ctx, pa)
+            c, ms = sp.spfhe_tune_ntt_chunk(ctx, rec.L - 1, items, NTT_CHUNKS)
+            for cc, t in zip(NTT_CHUNKS, ms):
+                timings["%d/%d/%d" % (var, pa, cc)] = round(t, 3)
+            if best is None or min(ms) < best[3]:
+                best = (var, pa, c, min(ms))
+    set_ntt(sp, ctx, best[:3])
+    return best[:3], timings
+
+
+def set_ntt(sp, ctx, cfg):
+    var, pa, chunk = cfg
+    sp.spfhe_ctx_set_ntt_variant(ctx, var)
+    sp.spfhe_ctx_set_ntt_split(ctx, pa)
+    sp.spfhe_ctx_set_ntt_chunk(ctx, chunk)
+
+
 class GpuMatmul:
     """Keys, encrypted operands and the matmul call for one workload."""
 
-    def __init__(self, case, rot_base, stream):
+    def __init__(self, case, rot_base, stream, ntt_chunk=-1):
         from paper_2604_11659_gb300 import params as gparams
         from paper_2604_11659_gb300 import spfhe
         self.sp = spfhe
@@ -138,6 +173,7 @@ class GpuMatmul:
         self.gp = gparams.ctx_params(rec, rot_base=rot_base)
         self.K = self.gp.K
         self.ctx = spfhe.spfhe_ctx_create(self.gp, stream)
+        self.ntt_chunk, self.ntt_tune = tune_ntt(spfhe, self.ctx, rec, ntt_chunk)
         self.n = 1 << rec.log_n
         self.S = self.n // 2
         t = time.time()
@@ -212,7 +248,7 @@ def _encrypt_case(sp, ctx, keys, case, level, scale, seed):
     return Am, enc(Ad, seed), Bm, enc(Bd, seed + 500), max(1, -(-(case.A.shape[0] * case.B.shape[1]) // S))
 
 
-def batch_vs_plain(stream, count, dims, seed=2):
+def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
     """`count` products of the batch workload's recipe (d from `dims`,
     sparsity U[0.70, 0.95], half Bernoulli / half 2:4) on its ring (N=2^16,
     L=20, dnum=4): one spfhe_sparse_matmul_batch call against one
@@ -224,6 +260,7 @@ def batch_vs_plain(stream, count, dims, seed=2):
     cases = synthetic.batch64_cases(seed=seed, count=count, dims=dims)
     rec = cases[0].ring
     ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    set_ntt(sp, ctx, ntt)
     keys = sp.spfhe_keygen(ctx, 99)
     prods = [_encrypt_case(sp, ctx, keys, c, rec.L, rec.scale, 10 * i) for i, c in enumerate(cases)]
     reqs = [sp.matmul_req(keys, Am, a, Bm, b) for Am, a, Bm, b, _ in prods]
@@ -275,7 +312,7 @@ def batch_vs_plain(stream, count, dims, seed=2):
             "speedup_over_per_product_batching": res["per_product"] / res["batched"]}
 
 
-def serve_run(stream, count, dims, rate, seed=4):
+def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
     """Poisson stream of `count` requests (d from `dims`, sparsity U[0.5,0.95],
     remaining levels U{10..30}, 4 key sets) on the serving ring (N=2^16, L=31,
     dnum=4): the continuous-batching server against a plain loop that runs each
@@ -287,6 +324,7 @@ def serve_run(stream, count, dims, rate, seed=4):
     reqs = synthetic.serving_stream(seed=seed, count=count, dims=dims, rate_per_s=rate)
     rec = reqs[0].case.ring
     ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    set_ntt(sp, ctx, ntt)
     keysets = [sp.spfhe_keygen(ctx, 700 + k) for k in range(4)]
     prods = [_encrypt_case(sp, ctx, keysets[r.key_set], r.case, r.level, rec.scale, 10 * i) for i, r in enumerate(reqs)]
     torch.cuda.synchronize()
@@ -446,20 +484,29 @@ def run_small_case(args):
     """Profiler case that stays small (a few GB on the device): a 128x128
     product at 99.5% sparsity on the workload's ring (N=2^16, L=24, dnum=3)
     through the same Alg. 1 + Alg. 2 executor, 4 matches per batch, rotation
-    base 2 (15 rotation keys).  Every kernel of the timed step runs with the
-    same per-limb shapes; the key-switching buffers (4 x 93 limbs of 512 KiB)
-    exceed the 129 MB L2."""
+    base 2 (15 rotation keys), --small-batch matches per batch (default 8).
+    Every kernel of the timed step runs with the same per-limb shapes; the
+    key-switching buffers (8 x 93 limbs of 512 KiB) exceed the 129 MB L2."""
     import torch
     from paper_2604_11659_gb300 import build as gbuild
     from paper_2604_11659_gb300 import synthetic
     gbuild.build()
-    os.environ["SPFHE_MATCH_BATCH"] = "4"
     rng = np.random.default_rng(args.seed)
     A = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
     B = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
     case = synthetic.MatmulCase("small", A, B, synthetic.ring_128x128())
-    g = GpuMatmul(case, 2, torch.cuda.current_stream().cuda_stream)
+    g = GpuMatmul(case, 2, torch.cuda.current_stream().cuda_stream, ntt_chunk=args.ntt_chunk)
+    g.sp.spfhe_ctx_set_match_batch(g.ctx, args.small_batch)
+    # the product alone sits in an NVTX range "product" (ncu --nvtx-include)
+    try:
+        torch.cuda.nvtx.range_push("product")
+        pushed = True
+    except Exception:
+        pushed = False
     outs, st = g.step()
+    torch.cuda.synchronize()
+    if pushed:
+        torch.cuda.nvtx.range_pop()
     err = g.check(outs)
     g.free(outs)
     print("small case done: %d matches, max err %.2e" % (st["matches"], err))
@@ -479,6 +526,9 @@ def main():
     ap.add_argument("--batch-products", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--ntt-chunk", type=int, default=-1,
+                    help="limbs per NTT launch pair; -1 = autotune on the workload's key-switch shape")
+    ap.add_argument("--small-batch", type=int, default=8)
     ap.add_argument("--small-case", action="store_true",
                     help="profiler case: three relinearised products (tensor + key switch) at the workload's ring")
     args = ap.parse_args()
@@ -509,7 +559,7 @@ def main():
     gbuild.build()
     stream = torch.cuda.current_stream().cuda_stream
     case = make_workload(args.workload, args.seed + rank)
-    g = GpuMatmul(case, args.rot_base, stream)
+    g = GpuMatmul(case, args.rot_base, stream, ntt_chunk=args.ntt_chunk)
     sp = g.sp
 
     for _ in range(max(3, args.warmup)):
@@ -612,6 +662,7 @@ def main():
                        % (args.workload, round(100 * (1 - g.nnz[0] / (g.rows * g.inner))), g.rec.log_n, Lr,
                           g.rec.dnum, g.K, args.rot_base),
                        "matches": st["matches"], "ks_per_step": st["ks_relin"] + st["ks_align"] + st["ks_final"],
+                       "ntt_variant_split_chunk": list(g.ntt_chunk), "ntt_tuning_ms": g.ntt_tune,
                        "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},
             "e2e": {"value": e2e_val, "unit": "matmuls/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
@@ -626,9 +677,9 @@ def main():
         sp.spfhe_ct_free(hnd)
     sp.spfhe_ctx_destroy(g.ctx)
     if args.batch_products > 0:
-        line["batch"] = batch_vs_plain(stream, args.batch_products, (8, 16))
+        line["batch"] = batch_vs_plain(stream, args.batch_products, (8, 16), ntt=g.ntt_chunk)
     if args.serve_requests > 0:
-        line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate)
+        line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(case, args.rot_base)
     if rank == 0:

@@ -74,9 +74,9 @@ typedef struct spfhe_pt spfhe_pt;
 typedef struct {
     uint32_t log_n;          /* ring degree n = 2^log_n, 2 <= log_n <= 17 */
     uint32_t L;              /* number of q primes (top level), 3 <= L <= 64 */
-    const uint32_t *q_bits;  /* L bit sizes: q_0 then the scaling primes; each in [20, 61] */
+    const uint32_t *q_bits;  /* L bit sizes: q_0 then the scaling primes; each in [20, 60] */
     uint32_t K;              /* number of special primes, 1 <= K <= 16 */
-    uint32_t p_bits;         /* bit size of each special prime, in [20, 61] */
+    uint32_t p_bits;         /* bit size of each special prime, in [20, 60] */
     uint32_t dnum;           /* key-switching digits; alpha = ceil(L/dnum) limbs per digit */
     double scale;            /* encoding scale Delta of fresh ciphertexts */
     uint32_t rot_base;       /* rotation plan base b (power of two >= 2) */
@@ -127,6 +127,27 @@ spfhe_status spfhe_sync(spfhe_ctx *ctx);
  * batches share each relinearisation key stream over more matches and need
  * about 320 MB of batch buffers per match at n = 2^16, L = 24. */
 spfhe_status spfhe_ctx_set_match_batch(spfhe_ctx *ctx, uint32_t matches);
+
+/* Limbs per launch pair of the two-pass NTT (n >= 2^12): a batch of
+ * transforms is cut into pieces of at most this many limbs, each running
+ * both passes before the next piece starts, so that the second pass reads
+ * the first pass's output from L2.  0 (default) = one launch pair for the
+ * whole batch; 1 .. 2^20 otherwise.  Results do not depend on it. */
+spfhe_status spfhe_ctx_set_ntt_chunk(spfhe_ctx *ctx, uint32_t limbs);
+
+/* Stages of the first pass of the two-pass NTT (n >= 2^12; the second pass
+ * takes the other log_n - pass_a_stages); both passes must have 6 to 9
+ * stages, else EINVAL.  0 (default) = log_n / 2.  Results do not depend on
+ * it. */
+spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
+
+/* Kernel variant of the two-pass NTT (n >= 2^12): 0 (default) = twiddles
+ * read per butterfly stage from global memory at 3 CTAs per SM; 1 = the same
+ * with the register budget of 2 CTAs per SM; 2 = as 1, with the second pass
+ * copying its twiddles into shared memory asynchronously before its data
+ * loads (about 64 KB of dynamic shared memory per CTA).  EINVAL otherwise.
+ * Results do not depend on it. */
+spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
 /* Number of kernels the library has launched since the context was created. */
 uint64_t spfhe_launch_count(const spfhe_ctx *ctx);
@@ -283,6 +304,19 @@ spfhe_status spfhe_sparse_matmul_ct_pt(spfhe_ctx *ctx, const spfhe_keys *keys,
                                        const spfhe_sparse_meta *B_csc, const double *B_values,
                                        spfhe_pt *const *B_pts, spfhe_ct **C_chunks, size_t n_c,
                                        spfhe_stats *stats);
+
+/* NTT launch-chunk tuner (library extension; the paper has no tuner).  Times
+ * the key-switching transforms of one match batch at level ell (forward NTT
+ * of the ModUp extension of `items` polynomials, inverse NTT of their ell
+ * input limbs) on scratch device buffers, three repetitions after one
+ * warm-up, for each of the n_candidates chunk sizes (see
+ * spfhe_ctx_set_ntt_chunk), sets the fastest on the context and returns it
+ * in *best; ms (n_candidates entries, may be NULL) receives the time per
+ * repetition.  Blocks the host; allocates and frees its buffers on the
+ * context stream.  EINVAL for bad shapes or candidates, ENOMEM when the
+ * buffers do not fit. */
+spfhe_status spfhe_tune_ntt_chunk(spfhe_ctx *ctx, uint32_t ell, uint32_t items, const uint32_t *candidates,
+                                  uint32_t n_candidates, uint32_t *best, double *ms);
 
 /* Rotation-plan base tuner (host only, no GPU work).  For the product A x B
  * (Alg. 1's plan on the metadata) at ring degree 2^log_n with L, K, dnum,

@@ -159,6 +159,38 @@ spfhe_status spfhe_ctx_set_match_batch(spfhe_ctx *ctx, uint32_t matches)
     });
 }
 
+spfhe_status spfhe_ctx_set_ntt_chunk(spfhe_ctx *ctx, uint32_t limbs)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        need(limbs <= (1u << 20), "chunk out of range");
+        ctx->c.ntt_chunk = (int)limbs;
+    });
+}
+
+spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        Ctx &c = ctx->c;
+        if (pass_a_stages != 0) {
+            const int pb = c.log_n - (int)pass_a_stages;
+            need(c.log_n >= 12 && pass_a_stages >= 6 && pass_a_stages <= 9 && pb >= 6 && pb <= 9,
+                 "both NTT passes need 6 to 9 stages");
+        }
+        c.ntt_pa = (int)pass_a_stages;
+    });
+}
+
+spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        need(variant <= 2, "NTT variant must be 0, 1 or 2");
+        ctx->c.ntt_variant = (int)variant;
+    });
+}
+
 spfhe_status spfhe_prof_enable(spfhe_ctx *ctx, int enable)
 {
     return guard([&] {

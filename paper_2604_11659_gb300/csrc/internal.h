@@ -46,15 +46,17 @@ struct DevTables {
     // ModUp basis conversion, one table per digit source set (indexed by the
     // digit's last limb + 1 = hi, 1..L): for source limb i of the digit
     // hat_inv[(hi-1)*alpha + i] (Shoup pair) and for every target modulus t
-    // hat_mont[((hi-1)*alpha + i) * M + t] = (D/q_i mod m_t) * 2^64 mod m_t.
-    u64 *mu_hat_inv = nullptr, *mu_hat_inv_p = nullptr, *mu_hat_mont = nullptr;
-    // digit modulus D = prod_{i in [lo, hi)} q_i modulo every target: [(hi-1) * M + t] (Shoup pair)
-    u64 *mu_dmod = nullptr, *mu_dmod_p = nullptr;
+    // hat_split[((hi-1)*alpha + i) * M + t] = (D/q_i mod m_t) * 2^64 mod m_t,
+    // split into 30-bit halves (low half in the low word).
+    u64 *mu_hat_inv = nullptr, *mu_hat_inv_p = nullptr, *mu_hat_split = nullptr;
+    // -D mod m_t in Montgomery form, split, with D = prod_{i in [lo, hi)} q_i: [(hi-1) * M + t]
+    u64 *mu_negd_split = nullptr;
     double *inv_q = nullptr;                       // [M] 1 / m (correctly rounded double)
-    // ModDown P -> Q: hat_inv over p_k, hat_mont[k * M + i], and P^{-1} mod q_i.
-    u64 *md_hat_inv = nullptr, *md_hat_inv_p = nullptr, *md_hat_mont = nullptr;
+    // ModDown P -> Q: hat_inv over p_k, hat_split[k * M + i] (as above), and
+    // P^{-1} mod q_i.
+    u64 *md_hat_inv = nullptr, *md_hat_inv_p = nullptr, *md_hat_split = nullptr;
     u64 *md_pinv = nullptr, *md_pinv_p = nullptr;   // [L]
-    u64 *md_pmod = nullptr, *md_pmod_p = nullptr;   // [L] P mod q_i (Shoup pair)
+    u64 *md_negp_split = nullptr;                   // [L] -P mod q_i in Montgomery form, split
     // Rescale dropping q_t: rs_inv[t * L + i] = q_t^{-1} mod q_i (Shoup pair),
     // rs_qt[t * L + i] = q_t mod q_i.
     u64 *rs_inv = nullptr, *rs_inv_p = nullptr, *rs_qt = nullptr;
@@ -103,6 +105,9 @@ struct Ctx {
     Prof prof;
     int in_keyswitch = 0;            // NTT launches inside key switching are classed separately
     int match_batch = 0;             // matches per batch (0: default for the ring size)
+    int ntt_chunk = 0;               // limbs per pass-A/pass-B launch pair (0: whole batch)
+    int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
+    int ntt_variant = 0;             // radix-16 kernel variant (0, 1, 2)
 };
 
 struct Keys {

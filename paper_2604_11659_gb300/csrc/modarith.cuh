@@ -61,6 +61,45 @@ __device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
     return x * w - h * q;
 }
 
+// Shoup multiplication with a truncated quotient: of the four 32x32-bit
+// partial products of x * w', the lowest (x0 w'0) is dropped, so the quotient
+// estimate is floor(x w' / 2^64) or one less and the result
+// x*w - Q'*q mod 2^64 lies in [0, 3q) for any x < 2^64.  Five wide and four
+// low 32-bit multiplies in all; nq = 2^64 - q.
+__device__ __forceinline__ u64 mul_shoup3(u64 x, u64 w, u64 wp, u64 nq)
+{
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 x0, x1, a0, a1, w0, w1, n0, n1, t0, t1, p0, p1, s1, q0, q1, r0, r1;\n\t"
+        ".reg .u64 t, p, s, qq, acc;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\t"
+        "mov.b64 {a0, a1}, %3;\n\t"
+        "mul.wide.u32 t, x1, a0;\n\t"
+        "mul.wide.u32 p, x0, a1;\n\t"
+        "mov.b64 {t0, t1}, t;\n\t"
+        "mov.b64 {p0, p1}, p;\n\t"
+        "add.cc.u32 t0, t0, p0;\n\t"
+        "addc.cc.u32 t1, t1, p1;\n\t"
+        "addc.u32 s1, 0, 0;\n\t"
+        "mov.b64 s, {t1, s1};\n\t"
+        "mad.wide.u32 qq, x1, a1, s;\n\t"
+        "mov.b64 {q0, q1}, qq;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.wide.u32 acc, x0, w0;\n\t"
+        "mad.wide.u32 acc, q0, n0, acc;\n\t"
+        "mov.b64 {r0, r1}, acc;\n\t"
+        "mad.lo.u32 r1, x0, w1, r1;\n\t"
+        "mad.lo.u32 r1, x1, w0, r1;\n\t"
+        "mad.lo.u32 r1, q0, n1, r1;\n\t"
+        "mad.lo.u32 r1, q1, n0, r1;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(x), "l"(w), "l"(wp), "l"(nq));
+    return r;
+}
+
 // Montgomery reduction of T = (hi, lo) < q * 2^64: returns T * 2^-64 mod q in [0, q)
 __device__ __forceinline__ u64 redc(U128 t, u64 q, u64 qneg_inv)
 {
@@ -74,6 +113,65 @@ __device__ __forceinline__ u64 redc(U128 t, u64 q, u64 qneg_inv)
     return csub(r, q);
 }
 
+// Carry-free sums of products of operands below 2^60 (base conversions and
+// the key-switching inner product).  Each operand is split into 30-bit
+// halves x = x1 2^30 + x0, each half product is below 2^60, and the four
+// partial-product classes are summed in separate 64-bit words:
+//   T = s00 + (s01 + s10) 2^30 + s11 2^60,
+// exact for up to 16 terms per word.  A constant stored "split" holds
+// x0 in its low 32-bit word and x1 in its high word.
+struct Acc30 {
+    u64 s00, s01, s10, s11;
+};
+
+__device__ __forceinline__ void acc30_zero(Acc30 &a) { a.s00 = a.s01 = a.s10 = a.s11 = 0; }
+
+// a += x * c for x = (x0, x1) and a split constant c
+__device__ __forceinline__ void acc30_mac(Acc30 &a, uint32_t x0, uint32_t x1, u64 c)
+{
+    const uint32_t c0 = (uint32_t)c, c1 = (uint32_t)(c >> 32);
+    asm("mad.wide.u32 %0, %4, %6, %0;\n\t"
+        "mad.wide.u32 %1, %4, %7, %1;\n\t"
+        "mad.wide.u32 %2, %5, %6, %2;\n\t"
+        "mad.wide.u32 %3, %5, %7, %3;"
+        : "+l"(a.s00), "+l"(a.s01), "+l"(a.s10), "+l"(a.s11)
+        : "r"(x0), "r"(x1), "r"(c0), "r"(c1));
+}
+
+// a += x * c for a small x < 2^30 (x1 = 0)
+__device__ __forceinline__ void acc30_mac_small(Acc30 &a, uint32_t x, u64 c)
+{
+    const uint32_t c0 = (uint32_t)c, c1 = (uint32_t)(c >> 32);
+    asm("mad.wide.u32 %0, %2, %3, %0;\n\t"
+        "mad.wide.u32 %1, %2, %4, %1;"
+        : "+l"(a.s00), "+l"(a.s01)
+        : "r"(x), "r"(c0), "r"(c1));
+}
+
+__device__ __forceinline__ void split30(u64 x, uint32_t &x0, uint32_t &x1)
+{
+    x0 = (uint32_t)x & 0x3fffffffu;
+    x1 = (uint32_t)(x >> 30);
+}
+
+// The 128-bit value T of an accumulator.
+__device__ __forceinline__ U128 acc30_value(const Acc30 &a)
+{
+    // mid = s01 + s10 as a 65-bit value (carry in mc)
+    const u64 mid = a.s01 + a.s10;
+    const u64 mc = mid < a.s01 ? 1ull : 0ull;
+    U128 t;
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u64 %1, %4, %5;"
+        : "=l"(t.lo), "=l"(t.hi)
+        : "l"(a.s00), "l"(mid << 30), "l"(mid >> 34), "l"(a.s11 >> 4));
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, %3;"
+        : "+l"(t.lo), "+l"(t.hi)
+        : "l"(a.s11 << 60), "l"(mc << 30));
+    return t;
+}
+
 // Per-modulus constants (device copy of the host table).
 struct ModConst {
     u64 q;
@@ -83,8 +181,11 @@ struct ModConst {
     u64 r2_mod;     // 2^128 mod q     (converts into Montgomery form via REDC)
     u64 n_inv;      // n^{-1} mod q (Shoup pair)
     u64 n_inv_p;
-    u64 pad;
+    u64 one_p;      // floor(2^64 / q): Shoup companion of 1 (reduces any x < 2^64)
 };
+
+// any x < 2^64 -> [0, q) (Shoup multiplication by 1)
+__device__ __forceinline__ u64 reduce_any(u64 x, u64 q, u64 one_p) { return csub(x - __umul64hi(x, one_p) * q, q); }
 
 // a * b mod q for two variable operands (REDC then undo the 2^-64 factor)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const ModConst &m)

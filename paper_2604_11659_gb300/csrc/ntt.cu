@@ -234,58 +234,103 @@ template <int P> __device__ __forceinline__ int r16_tw(int j, int ls, int stage0
     return (1 << (stage0 + ls)) + (btile << ls) + (j >> (P - ls));
 }
 
-// Harvey's lazy butterflies: forward values stay in [0, 4q) (x is brought to
-// [0, 2q) first, w*y is taken in [0, 2q)), inverse values in [0, 2q); only
-// the last pass reduces to [0, q).  Needs 4q < 2^64.
-template <int P, int RND>
+// Stage l of a round pairs register bit Q-1-l; the twiddle of a butterfly
+// depends on the register index only through i >> (Q - l), so each stage
+// loads its 16 >> (Q - l) distinct (twiddle, companion) pairs once, from
+// global memory or (SM, pass B) from the CTA's shared-memory copy.
+//
+// Shared-memory twiddles of pass B: the CTA's T = 4096 >> P tiles need, at
+// pass-local stage ls, the contiguous entries 2^(PA+ls) + b0 2^ls + [0, T 2^ls)
+// (b0 = the CTA's first tile); they are kept at offset T (2^ls - 1).
+template <int P> __host__ __device__ constexpr int r16_tw_smem_entries() { return (kElems >> P) * ((1 << P) - 1); }
+
+template <int P, int RND, int Q, int l, bool SM>
+__device__ __forceinline__ void r16_load_tw(ulonglong2 (&wt)[16], int t, const ulonglong2 *__restrict__ w2,
+                                            int stage0, int btile, const ulonglong2 *smt, int ltile)
+{
+    constexpr int G = 16 >> (Q - l);
+    constexpr int ls = 4 * RND + l;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = r16_index<P, RND>(t, g << (Q - l));
+        if constexpr (SM) wt[g] = smt[(kElems >> P) * ((1 << ls) - 1) + (ltile << ls) + (j >> (P - ls))];
+        else wt[g] = __ldg(w2 + r16_tw<P>(j, ls, stage0, btile));
+    }
+}
+
+// Products w*y are taken in [0, 3q) for any y < 2^64 (mul_shoup3).
+// LAZY (q < 2^58): no reduction of x at all; every stage raises the bound on
+// all values by 3q, so after the log_n <= 17 stages of both passes they lie
+// in [0, 52q) (< 2^64) and pass B reduces them once at the end.  Otherwise
+// values stay in [0, 6q): x is first brought to [0, 3q).
+template <int P, int RND, int l, bool LAZY, bool SM>
+__device__ __forceinline__ void r16_fwd_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
+                                              int stage0, int btile, const ulonglong2 *smt, int ltile)
+{
+    constexpr int Q = r16_q<P, RND>();
+    constexpr int half = 1 << (Q - 1 - l);
+    const u64 q3 = 3 * q, nq = 0 - q;
+    ulonglong2 wt[16];
+    r16_load_tw<P, RND, Q, l, SM>(wt, t, w2, stage0, btile, smt, ltile);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i & half) continue;
+        const ulonglong2 w = wt[i >> (Q - l)];
+        const u64 x = LAZY ? v[i] : csub(v[i], q3);
+        const u64 y = mul_shoup3(v[i + half], w.x, w.y, nq);
+        v[i] = x + y;
+        v[i + half] = x - y + q3;
+    }
+}
+
+template <int P, int RND, int l, bool SM>
+__device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
+                                              int stage0, int btile, const ulonglong2 *smt, int ltile)
+{
+    constexpr int Q = r16_q<P, RND>();
+    constexpr int half = 1 << (Q - 1 - l);
+    const u64 q3 = 3 * q, nq = 0 - q;
+    ulonglong2 wt[16];
+    r16_load_tw<P, RND, Q, l, SM>(wt, t, w2, stage0, btile, smt, ltile);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i & half) continue;
+        const ulonglong2 w = wt[i >> (Q - l)];
+        const u64 x = v[i], y = v[i + half];
+        v[i] = csub(x + y, q3);
+        v[i + half] = mul_shoup3(x - y + q3, w.x, w.y, nq);
+    }
+}
+
+// Lazy butterflies (Harvey's scheme with the [0, 3q) products of
+// mul_shoup3): forward values stay below 6q (52q on the reduction-free path),
+// inverse values in [0, 3q); only the last pass reduces to [0, q).
+template <int P, int RND, bool LAZY, bool SM = false>
 __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
-                                              int stage0, int btile)
+                                              int stage0, int btile, const ulonglong2 *smt = nullptr,
+                                              int ltile = 0)
 {
     constexpr int Q = r16_q<P, RND>();
-    const u64 q2 = 2 * q;
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-        const int half = 1 << (Q - 1 - l);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i & half) continue;
-            const int j = r16_index<P, RND>(t, i);
-            const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
-            const ulonglong2 wt = __ldg(w2 + ti);
-            const u64 W = wt.x, Wp = wt.y;
-            const u64 x = csub(v[i], q2);
-            const u64 y = mul_shoup_lazy(v[i + half], W, Wp, q);
-            v[i] = x + y;
-            v[i + half] = x - y + q2;
-        }
-    }
+    r16_fwd_stage<P, RND, 0, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 1) r16_fwd_stage<P, RND, 1, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 2) r16_fwd_stage<P, RND, 2, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 3) r16_fwd_stage<P, RND, 3, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
 }
 
-template <int P, int RND>
+// moduli below this take the reduction-free forward butterflies
+constexpr u64 kLazyFwdBound = 1ull << 58;
+
+template <int P, int RND, bool SM = false>
 __device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
-                                              int stage0, int btile)
+                                              int stage0, int btile, const ulonglong2 *smt = nullptr,
+                                              int ltile = 0)
 {
     constexpr int Q = r16_q<P, RND>();
-    const u64 q2 = 2 * q;
-#pragma unroll
-    for (int l = Q - 1; l >= 0; --l) {
-        const int half = 1 << (Q - 1 - l);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i & half) continue;
-            const int j = r16_index<P, RND>(t, i);
-            const int ti = r16_tw<P>(j, 4 * RND + l, stage0, btile);
-            const ulonglong2 wt = __ldg(w2 + ti);
-            const u64 W = wt.x, Wp = wt.y;
-            const u64 x = v[i], y = v[i + half];
-            v[i] = csub(x + y, q2);
-            v[i + half] = mul_shoup_lazy(x - y + q2, W, Wp, q);
-        }
-    }
+    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    r16_inv_stage<P, RND, 0, SM>(v, t, w2, q, stage0, btile, smt, ltile);
 }
-
-// [0, 4q) -> [0, q)
-__device__ __forceinline__ u64 reduce4(u64 x, u64 q) { return csub(csub(x, 2 * q), q); }
 
 // shared-memory slot of tile element j (pass B layout; pad one word per 16)
 template <int P> __device__ __forceinline__ int r16_slot_b(int tile, int j)
@@ -300,32 +345,55 @@ template <int P> __device__ __forceinline__ int r16_slot_a(int col, int row)
 template <int P> constexpr int r16_smem_words_a() { return kElems + (((1 << P) >> 4) << 3); }
 template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4); }
 
+// Kernel variants (picked per context, see spfhe_ctx_set_ntt_variant):
+//   0: twiddles loaded per stage from global memory, 3 CTAs per SM;
+//   1: the same with the register budget of 2 CTAs per SM;
+//   2: as 1, and pass B copies its CTA's twiddles into shared memory with
+//      asynchronous copies issued before its data loads.
+template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : 2; }
+
+// Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
-__global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const ulonglong2 *__restrict__ tw2, int log_n)
+__device__ __forceinline__ void r16_prefetch_tw(ulonglong2 *smt, const ulonglong2 *__restrict__ w2, int PA, int b0)
 {
-    __shared__ u64 sm[r16_smem_words_a<P>()];
+    constexpr int T = kElems >> P;
+#pragma unroll 1
+    for (int ls = 0; ls < P; ++ls) {
+        const ulonglong2 *src = w2 + ((size_t)1 << (PA + ls)) + ((size_t)b0 << ls);
+        ulonglong2 *dst = smt + T * ((1 << ls) - 1);
+        for (int x = threadIdx.x; x < (T << ls); x += 256) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + x);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + x) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void r16_prefetch_wait()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
+template <int P, bool LAZY>
+__device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n)
+{
     constexpr int TPC = kElems >> P;   // columns per CTA
     constexpr int R = (P + 3) / 4;
-    const int n = 1 << log_n;
-    int mi;
-    u64 *p = limb_ptr(a, n, mi);
-    const u64 q = mc[mi].q;
-    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int lg_ncols = log_n - P;
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
-    r16_fwd_round<P, 0>(v, t, w2, q, 0, 0);
+    r16_fwd_round<P, 0, LAZY>(v, t, w2, q, 0, 0);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 1, LAZY>(v, t, w2, q, 0, 0);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -334,25 +402,33 @@ __global__ void __launch_bounds__(256) k_fwd16_a(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 2, LAZY>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const ulonglong2 *__restrict__ tw2, int log_n,
-                                                 int PA)
+template <int P, int V>
+__global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a, const ModConst *__restrict__ mc,
+                                                                      const ulonglong2 *__restrict__ tw2, int log_n)
 {
-    __shared__ u64 sm[r16_smem_words_b<P>()];
-    constexpr int TPT = 1 << (P - 4);  // threads per tile
-    constexpr int R = (P + 3) / 4;
+    __shared__ u64 sm[r16_smem_words_a<P>()];
     const int n = 1 << log_n;
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
+    if (q < kLazyFwdBound) fwd16_a_body<P, true>(sm, p, q, w2, log_n);
+    else fwd16_a_body<P, false>(sm, p, q, w2, log_n);
+}
+
+template <int P, bool LAZY, bool SM>
+__device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m, const ulonglong2 *__restrict__ w2,
+                                             int PA, const ulonglong2 *smt)
+{
+    constexpr int TPT = 1 << (P - 4);  // threads per tile
+    constexpr int R = (P + 3) / 4;
+    const u64 q = m.q;
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
     const size_t e0 = (size_t)blockIdx.x * kElems;
     const int btile = (int)(e0 >> P) + tile;
@@ -360,14 +436,15 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = tp[r16_index<P, 0>(t, i)];
-    r16_fwd_round<P, 0>(v, t, w2, q, PA, btile);
+    if constexpr (SM) r16_prefetch_wait();
+    r16_fwd_round<P, 0, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1>(v, t, w2, q, PA, btile);
+        r16_fwd_round<P, 1, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -376,7 +453,7 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2>(v, t, w2, q, PA, btile);
+        r16_fwd_round<P, 2, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
     }
     // the last round holds 16 contiguous elements per thread: stage through
     // shared memory so the global stores are coalesced
@@ -384,15 +461,42 @@ __global__ void __launch_bounds__(256) k_fwd16_b(NttArgs a, const ModConst *__re
 #pragma unroll
     for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
     __syncthreads();
-    for (int x = threadIdx.x; x < kElems; x += 256) p[e0 + x] = reduce4(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q);
+    for (int x = threadIdx.x; x < kElems; x += 256) {
+        const u64 y = sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))];
+        p[e0 + x] = reduce_any(y, q, m.one_p);
+    }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const ulonglong2 *__restrict__ tw2,
-                                                 int log_n, int PA)
+template <int P, int V>
+__global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a, const ModConst *__restrict__ mc,
+                                                                      const ulonglong2 *__restrict__ tw2, int log_n,
+                                                                      int PA)
 {
     __shared__ u64 sm[r16_smem_words_b<P>()];
+    extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
+    const int n = 1 << log_n;
+    int mi;
+    u64 *p = limb_ptr(a, n, mi);
+    const ModConst m = mc[mi];
+    const ulonglong2 *w2 = tw2 + (size_t)mi * n;
+    if constexpr (V == 2) {
+        r16_prefetch_tw<P>(smt, w2, PA, (int)(((size_t)blockIdx.x * kElems) >> P));
+        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
+        else fwd16_b_body<P, false, true>(sm, p, m, w2, PA, smt);
+    } else {
+        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false>(sm, p, m, w2, PA, nullptr);
+        else fwd16_b_body<P, false, false>(sm, p, m, w2, PA, nullptr);
+    }
+}
+
+template <int P, int V>
+__global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a, const ModConst *__restrict__ mc,
+                                                                      const ulonglong2 *__restrict__ tw2, int log_n,
+                                                                      int PA)
+{
+    __shared__ u64 sm[r16_smem_words_b<P>()];
+    extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
+    constexpr bool SM = V == 2;
     constexpr int TPT = 1 << (P - 4);
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
@@ -403,12 +507,14 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
     const size_t e0 = (size_t)blockIdx.x * kElems;
     const int btile = (int)(e0 >> P) + tile;
+    if constexpr (SM) r16_prefetch_tw<P>(smt, w2, PA, (int)(e0 >> P));
     for (int x = threadIdx.x; x < kElems; x += 256) sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = p[e0 + x];
-    __syncthreads();
+    if constexpr (SM) r16_prefetch_wait();
+    else __syncthreads();
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
-    r16_inv_round<P, R - 1>(v, t, w2, q, PA, btile);
+    r16_inv_round<P, R - 1, SM>(v, t, w2, q, PA, btile, smt, tile);
     if constexpr (R > 2) {
         __syncthreads();
 #pragma unroll
@@ -416,7 +522,7 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2>(v, t, w2, q, PA, btile);
+        r16_inv_round<P, R - 2, SM>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 1) {
         __syncthreads();
@@ -425,17 +531,16 @@ __global__ void __launch_bounds__(256) k_inv16_b(NttArgs a, const ModConst *__re
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0>(v, t, w2, q, PA, btile);
+        r16_inv_round<P, 0, SM>(v, t, w2, q, PA, btile, smt, tile);
     }
     u64 *tp = p + e0 + ((size_t)tile << P);
 #pragma unroll
     for (int i = 0; i < 16; ++i) tp[r16_index<P, 0>(t, i)] = v[i];
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__restrict__ mc,
-                                                 const ulonglong2 *__restrict__ tw2,
-                                                 int log_n)
+template <int P, int V>
+__global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a, const ModConst *__restrict__ mc,
+                                                                      const ulonglong2 *__restrict__ tw2, int log_n)
 {
     __shared__ u64 sm[r16_smem_words_a<P>()];
     constexpr int TPC = kElems >> P;
@@ -475,22 +580,70 @@ __global__ void __launch_bounds__(256) k_inv16_a(NttArgs a, const ModConst *__re
         p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = mul_shoup(v[i], m.n_inv, m.n_inv_p, q);
 }
 
-template <int P> struct R16Launch {
+// dynamic shared memory of pass B for variant V (opted in once per kernel;
+// DIR tells the forward and inverse kernels apart, their types are equal)
+template <int P, int V, int DIR, typename K> size_t r16_b_smem(K kernel)
+{
+    if constexpr (V != 2) {
+        (void)kernel;
+        return 0;
+    } else {
+        const size_t bytes = (size_t)r16_tw_smem_entries<P>() * sizeof(ulonglong2);
+        static bool done = false;
+        if (!done) {
+            SPFHE_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            done = true;
+        }
+        return bytes;
+    }
+}
+
+template <int P, int V> struct R16LaunchV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
-        k_fwd16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n);
+        k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
     {
-        k_fwd16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA);
+        const size_t smem = r16_b_smem<P, V, 0>(k_fwd16_b<P, V>);
+        k_fwd16_b<P, V><<<g, 256, smem, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA);
     }
     static void inv_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
-        k_inv16_a<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n);
+        k_inv16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n);
     }
     static void inv_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
     {
-        k_inv16_b<P><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n, PA);
+        const size_t smem = r16_b_smem<P, V, 1>(k_inv16_b<P, V>);
+        k_inv16_b<P, V><<<g, 256, smem, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n, PA);
+    }
+};
+
+template <int P> struct R16Launch {
+    template <typename F> static void variant(int v, F &&f)
+    {
+        switch (v) {
+        case 0: f(R16LaunchV<P, 0>{}); break;
+        case 1: f(R16LaunchV<P, 1>{}); break;
+        case 2: f(R16LaunchV<P, 2>{}); break;
+        default: throw Error(SPFHE_EINVAL, "no such NTT variant");
+        }
+    }
+    static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
+    {
+        variant(c.ntt_variant, [&](auto L) { decltype(L)::fwd_a(g, s, a, c); });
+    }
+    static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
+    {
+        variant(c.ntt_variant, [&](auto L) { decltype(L)::fwd_b(g, s, a, c, PA); });
+    }
+    static void inv_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
+    {
+        variant(c.ntt_variant, [&](auto L) { decltype(L)::inv_a(g, s, a, c); });
+    }
+    static void inv_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
+    {
+        variant(c.ntt_variant, [&](auto L) { decltype(L)::inv_b(g, s, a, c, PA); });
     }
 };
 
@@ -534,6 +687,39 @@ void launch_checks(const Batch &b, const LimbMap &map)
     if (b.items > 65535) throw Error(SPFHE_EINVAL, "too many items in one NTT launch");
 }
 
+// Split a transform batch into launch pairs of at most ctx.ntt_chunk limbs,
+// so that pass B finds pass A's output in L2 (0 = one pair for the batch).
+template <typename F> void for_chunks(const Ctx &ctx, const Batch &b, const LimbMap &map, F &&f)
+{
+    const int chunk = ctx.ntt_chunk;
+    if (chunk <= 0 || (long long)map.nl * b.items <= chunk) {
+        f(b, map);
+        return;
+    }
+    auto item_batch = [&](int i0, int cnt) {
+        Batch s = b;
+        s.items = cnt;
+        if (b.ids) s.ids = b.ids + i0;
+        else s.base = b.base + (long long)i0 * b.stride;
+        return s;
+    };
+    if (map.nl <= chunk) {
+        const int per = chunk / map.nl;
+        for (int i0 = 0; i0 < b.items; i0 += per) f(item_batch(i0, std::min(per, b.items - i0)), map);
+        return;
+    }
+    for (int i0 = 0; i0 < b.items; ++i0)
+        for (int s0 = 0; s0 < map.nl; s0 += chunk) {
+            LimbMap m;
+            m.nl = std::min(chunk, map.nl - s0);
+            for (int k = 0; k < m.nl; ++k) {
+                m.off[k] = map.off[s0 + k];
+                m.mi[k] = map.mi[s0 + k];
+            }
+            f(item_batch(i0, 1), m);
+        }
+}
+
 }  // namespace
 
 LimbMap limb_range(int first_off, int count, int first_mi)
@@ -547,6 +733,9 @@ LimbMap limb_range(int first_off, int count, int first_mi)
     return m;
 }
 
+// stages in pass A of the radix-16 transforms (the rest run in pass B)
+static int pass_a_stages(const Ctx &ctx) { return ctx.ntt_pa ? ctx.ntt_pa : ctx.log_n / 2; }
+
 void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
 {
     launch_checks(b, map);
@@ -555,18 +744,21 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
     NttArgs a{b.base, b.stride, b.ids, map};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD;
     if (ctx.log_n >= 12) {
-        const int PA = ctx.log_n / 2, PB = ctx.log_n - PA;
-        dim3 grid(ctx.n / kElems, map.nl, b.items);
-        {
-            cudaEvent_t t0_ = prof_begin(ctx);
-            r16_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, a, ctx); });
-            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items, "ntt fwd A");
-        }
-        {
-            cudaEvent_t t0_ = prof_begin(ctx);
-            r16_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, a, ctx, PA); });
-            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PB * map.nl * b.items, "ntt fwd B");
-        }
+        const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
+        for_chunks(ctx, b, map, [&](const Batch &cb, const LimbMap &cm) {
+            NttArgs ca{cb.base, cb.stride, cb.ids, cm};
+            dim3 grid(ctx.n / kElems, cm.nl, cb.items);
+            {
+                cudaEvent_t t0_ = prof_begin(ctx);
+                r16_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, ca, ctx); });
+                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt fwd A");
+            }
+            {
+                cudaEvent_t t0_ = prof_begin(ctx);
+                r16_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, ca, ctx, PA); });
+                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt fwd B");
+            }
+        });
         return;
     }
     dim3 ga(g.grid_a, map.nl, b.items), gb(g.grid_b, map.nl, b.items);
@@ -590,18 +782,21 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
     NttArgs a{b.base, b.stride, b.ids, map};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV;
     if (ctx.log_n >= 12) {
-        const int PA = ctx.log_n / 2, PB = ctx.log_n - PA;
-        dim3 grid(ctx.n / kElems, map.nl, b.items);
-        {
-            cudaEvent_t t0_ = prof_begin(ctx);
-            r16_dispatch(PB, [&](auto L) { decltype(L)::inv_b(grid, ctx.stream, a, ctx, PA); });
-            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PB * map.nl * b.items, "ntt inv B");
-        }
-        {
-            cudaEvent_t t0_ = prof_begin(ctx);
-            r16_dispatch(PA, [&](auto L) { decltype(L)::inv_a(grid, ctx.stream, a, ctx); });
-            prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items, "ntt inv A");
-        }
+        const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
+        for_chunks(ctx, b, map, [&](const Batch &cb, const LimbMap &cm) {
+            NttArgs ca{cb.base, cb.stride, cb.ids, cm};
+            dim3 grid(ctx.n / kElems, cm.nl, cb.items);
+            {
+                cudaEvent_t t0_ = prof_begin(ctx);
+                r16_dispatch(PB, [&](auto L) { decltype(L)::inv_b(grid, ctx.stream, ca, ctx, PA); });
+                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt inv B");
+            }
+            {
+                cudaEvent_t t0_ = prof_begin(ctx);
+                r16_dispatch(PA, [&](auto L) { decltype(L)::inv_a(grid, ctx.stream, ca, ctx); });
+                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt inv A");
+            }
+        });
         return;
     }
     dim3 ga(g.grid_a, map.nl, b.items), gb(g.grid_b, map.nl, b.items);

@@ -27,6 +27,9 @@ u64 invmod_host(u64 a, u64 q) { return powmod_host(a, q - 2, q); }
 
 u64 shoup_pre(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
 
+// x < 2^60 as two 30-bit halves: low half in the low 32-bit word
+static u64 split30_host(u64 x) { return (x & 0x3fffffffull) | ((x >> 30) << 32); }
+
 // Miller-Rabin with the first twelve prime bases (exact for 64-bit inputs).
 static bool is_prime64(u64 n)
 {
@@ -89,11 +92,11 @@ void build_params(Ctx &ctx, const spfhe_params &p)
     if (p.L < 3 || p.L > 64 || !p.q_bits) throw Error(SPFHE_EPARAM, "L must be in [3, 64] with q_bits");
     if (p.K < 1 || p.K > 16 || p.L + p.K > (uint32_t)kMaxMods) throw Error(SPFHE_EPARAM, "K out of range");
     if (p.dnum < 1 || p.dnum > p.L) throw Error(SPFHE_EPARAM, "dnum must be in [1, L]");
-    if (p.p_bits < 20 || p.p_bits > 61) throw Error(SPFHE_EPARAM, "p_bits out of range");
+    if (p.p_bits < 20 || p.p_bits > 60) throw Error(SPFHE_EPARAM, "p_bits must be in [20, 60]");
     if (p.rot_base < 2 || (p.rot_base & (p.rot_base - 1))) throw Error(SPFHE_EPARAM, "rot_base must be a power of two");
     if (!(p.scale > 1.0)) throw Error(SPFHE_EPARAM, "scale must exceed 1");
     for (uint32_t i = 0; i < p.L; ++i)
-        if (p.q_bits[i] < 20 || p.q_bits[i] > 61) throw Error(SPFHE_EPARAM, "q_bits out of range");
+        if (p.q_bits[i] < 20 || p.q_bits[i] > 60) throw Error(SPFHE_EPARAM, "q_bits must be in [20, 60]");
     ctx.log_n = p.log_n;
     ctx.n = 1 << p.log_n;
     ctx.S = ctx.n / 2;
@@ -121,6 +124,7 @@ void build_params(Ctx &ctx, const spfhe_params &p)
         m.r2_mod = mulmod_host(m.r_mod, m.r_mod, q);
         m.n_inv = invmod_host((u64)ctx.n % q, q);
         m.n_inv_p = shoup_pre(m.n_inv, q);
+        m.one_p = shoup_pre(1, q);
         ctx.mc.push_back(m);
     }
 }
@@ -193,28 +197,27 @@ void upload_tables(Ctx &ctx)
             }
         }
     }
-    std::vector<u64> dmod((size_t)L * M), dmodp((size_t)L * M);
+    std::vector<u64> negd((size_t)L * M);
     for (int hi = 1; hi <= L; ++hi) {
         const int lo = ((hi - 1) / A) * A;
         for (int tt = 0; tt < M; ++tt) {
             const u64 m = ctx.mods[tt];
             u64 d = 1 % m;
             for (int k = lo; k < hi; ++k) d = mulmod_host(d, ctx.mods[k] % m, m);
-            dmod[(size_t)(hi - 1) * M + tt] = d;
-            dmodp[(size_t)(hi - 1) * M + tt] = shoup_pre(d, m);
+            negd[(size_t)(hi - 1) * M + tt] = split30_host(mulmod_host((m - d) % m, ctx.mc[tt].r_mod, m));
         }
     }
-    t.mu_dmod = upload(dmod);
-    t.mu_dmod_p = upload(dmodp);
+    for (u64 &x : hmont) x = split30_host(x);
+    t.mu_negd_split = upload(negd);
     std::vector<double> invq(M);
     for (int i = 0; i < M; ++i) invq[i] = 1.0 / (double)ctx.mods[i];
     t.inv_q = upload(invq);
     t.mu_hat_inv = upload(hinv);
     t.mu_hat_inv_p = upload(hinvp);
-    t.mu_hat_mont = upload(hmont);
+    t.mu_hat_split = upload(hmont);
 
     // ModDown P -> Q
-    std::vector<u64> dinv(K), dinvp(K), dmont((size_t)K * M), pinv(L), pinvp(L), pmod(L), pmodp(L);
+    std::vector<u64> dinv(K), dinvp(K), dmont((size_t)K * M), pinv(L), pinvp(L), negp(L);
     for (int k = 0; k < K; ++k) {
         const u64 pk = ctx.mods[L + k];
         u64 d = 1;
@@ -227,7 +230,7 @@ void upload_tables(Ctx &ctx)
             u64 dm = 1 % m;
             for (int j = 0; j < K; ++j)
                 if (j != k) dm = mulmod_host(dm, ctx.mods[L + j] % m, m);
-            dmont[(size_t)k * M + tt] = mulmod_host(dm, ctx.mc[tt].r_mod, m);
+            dmont[(size_t)k * M + tt] = split30_host(mulmod_host(dm, ctx.mc[tt].r_mod, m));
         }
     }
     for (int i = 0; i < L; ++i) {
@@ -236,16 +239,14 @@ void upload_tables(Ctx &ctx)
         for (int k = 0; k < K; ++k) P = mulmod_host(P, ctx.mods[L + k] % qi, qi);
         pinv[i] = invmod_host(P, qi);
         pinvp[i] = shoup_pre(pinv[i], qi);
-        pmod[i] = P;
-        pmodp[i] = shoup_pre(P, qi);
+        negp[i] = split30_host(mulmod_host((qi - P) % qi, ctx.mc[i].r_mod, qi));
     }
     t.md_hat_inv = upload(dinv);
     t.md_hat_inv_p = upload(dinvp);
-    t.md_hat_mont = upload(dmont);
+    t.md_hat_split = upload(dmont);
     t.md_pinv = upload(pinv);
     t.md_pinv_p = upload(pinvp);
-    t.md_pmod = upload(pmod);
-    t.md_pmod_p = upload(pmodp);
+    t.md_negp_split = upload(negp);
 
     // Rescale
     std::vector<u64> rinv((size_t)L * L, 0), rinvp((size_t)L * L, 0), rqt((size_t)L * L, 0);
@@ -264,10 +265,9 @@ void upload_tables(Ctx &ctx)
 void free_tables(Ctx &ctx)
 {
     DevTables &t = ctx.dt;
-    u64 *ptrs[] = {t.tw, t.twp, t.itw, t.itwp, t.mu_hat_inv, t.mu_hat_inv_p, t.mu_hat_mont,
-                   t.md_hat_inv, t.md_hat_inv_p, t.md_hat_mont, t.md_pinv, t.md_pinv_p,
-                   t.md_pmod, t.md_pmod_p, t.mu_dmod, t.mu_dmod_p,
-                   t.rs_inv, t.rs_inv_p, t.rs_qt};
+    u64 *ptrs[] = {t.tw, t.twp, t.itw, t.itwp, t.mu_hat_inv, t.mu_hat_inv_p, t.mu_hat_split,
+                   t.md_hat_inv, t.md_hat_inv_p, t.md_hat_split, t.md_pinv, t.md_pinv_p,
+                   t.md_negp_split, t.mu_negd_split, t.rs_inv, t.rs_inv_p, t.rs_qt};
     for (u64 *p : ptrs)
         if (p) cudaFree(p);
     if (t.mc) cudaFree(t.mc);

@@ -53,53 +53,85 @@ __global__ void k_automorph(int polys, int ell, int log_n, const u64 *const *in,
     (void)ell;
 }
 
+// Base-conversion constant rows in shared memory: for every target modulus a
+// row of RL words [c_0 .. c_{NS-1}, c_corr, q, -q^{-1} mod 2^64 (, pad)]
+// (c's split, Montgomery form), RL even so rows are 16-byte aligned.
+template <int NS> constexpr int bconv_row() { return (NS + 3 + 1) & ~1; }
+
+template <int NS>
+__device__ __forceinline__ u64 bconv_out(const u64 *row, const uint32_t (&y0)[NS], const uint32_t (&y1)[NS],
+                                         uint32_t v)
+{
+    constexpr int RL = bconv_row<NS>();
+    const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(row);
+    Acc30 a;
+    acc30_zero(a);
+    u64 q = 0, qi = 0;
+#pragma unroll
+    for (int p = 0; p < RL / 2; ++p) {
+        const ulonglong2 w = r2[p];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = 2 * p + h;
+            const u64 c = h ? w.y : w.x;
+            if (e < NS) acc30_mac(a, y0[e < NS ? e : 0], y1[e < NS ? e : 0], c);
+            else if (e == NS) acc30_mac_small(a, v, c);
+            else if (e == NS + 1) q = c;
+            else if (e == NS + 2) qi = c;
+        }
+    }
+    return redc(acc30_value(a), q, qi);
+}
+
 // ModUp: for digit j (blockIdx.y) with source limbs [lo, hi) of the
 // coefficient-domain input, write the centred representative of the digit
 // value modulo D = prod q_i into every extended limb t outside [lo, hi):
 //   y_i = [x_i (D/q_i)^{-1}]_{q_i},  v = round(sum_i y_i / q_i) (fma chain),
-//   out_t = sum_i y_i (D/q_i) - v D  mod m_t.
+//   out_t = sum_i y_i (D/q_i) - v D  mod m_t,
+// one carry-free accumulation (Acc30) of NS + 1 products with Montgomery-form
+// constants (the last one v * (-D mod m_t)) and one REDC per output.
 // Extended limb t < ell is q_t, t >= ell is p_{t-ell} (modulus L + t - ell).
 template <int NS>
-__global__ void __launch_bounds__(256) k_modup_bconv(int digit0, int ell, int L, int K, int alpha, int M, int n,
-                                                     const u64 *coef,
-                                                     long long coef_stride, u64 *ext, long long ext_stride,
-                                                     const ModConst *__restrict__ mc, const u64 *__restrict__ hinv,
-                                                     const u64 *__restrict__ hinvp, const u64 *__restrict__ hmont,
-                                                     const u64 *__restrict__ dmod, const u64 *__restrict__ dmodp,
+__global__ void __launch_bounds__(256, 4) k_modup_bconv(int digit0, int ell, int L, int K, int alpha, int M, int n,
+                                                     const u64 *coef, long long coef_stride, u64 *ext,
+                                                     long long ext_stride, const ModConst *__restrict__ mc,
+                                                     const u64 *__restrict__ hinv, const u64 *__restrict__ hinvp,
+                                                     const u64 *__restrict__ hsplit, const u64 *__restrict__ negd,
                                                      const double *__restrict__ inv_q)
 {
-    extern __shared__ u64 sh[];   // [NS][M] constants
+    constexpr int RL = bconv_row<NS>();
+    extern __shared__ __align__(16) u64 sh[];   // [M][RL]
     const int j = digit0 + blockIdx.y, it = blockIdx.z;
     const int lo = j * alpha, hi = lo + NS;
     const size_t row0 = (size_t)(hi - 1) * alpha;
-    for (int x = threadIdx.x; x < NS * M; x += blockDim.x) sh[x] = hmont[row0 * M + x];
+    for (int x = threadIdx.x; x < M * RL; x += blockDim.x) {
+        const int gm = x / RL, c = x - gm * RL;
+        u64 w = 0;
+        if (c < NS) w = hsplit[(row0 + c) * M + gm];
+        else if (c == NS) w = negd[(size_t)(hi - 1) * M + gm];
+        else if (c == NS + 1) w = mc[gm].q;
+        else if (c == NS + 2) w = mc[gm].qneg_inv;
+        sh[x] = w;
+    }
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    u64 y[NS];
+    uint32_t y0[NS], y1[NS];
     double f = 0.0;
     const u64 *src = coef + it * coef_stride;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const u64 q = mc[lo + i].q;
-        y[i] = mul_shoup(src[(size_t)(lo + i) * n + k], __ldg(hinv + row0 + i), __ldg(hinvp + row0 + i), q);
-        f = fma((double)y[i], __ldg(inv_q + lo + i), f);
+        const u64 y = mul_shoup(src[(size_t)(lo + i) * n + k], __ldg(hinv + row0 + i), __ldg(hinvp + row0 + i), q);
+        f = fma((double)y, __ldg(inv_q + lo + i), f);
+        split30(y, y0[i], y1[i]);
     }
-    const u64 v = (u64)rint(f);
+    const uint32_t v = (uint32_t)rint(f);
     const int next = ell + K;
-    const u64 *dm = dmod + (size_t)(hi - 1) * M;
-    const u64 *dmp = dmodp + (size_t)(hi - 1) * M;
     u64 *dst = ext + it * ext_stride + (size_t)j * next * n + k;
-    for (int t = 0; t < next; ++t) {
-        if (t >= lo && t < hi) continue;
-        const int gm = t < ell ? t : L + (t - ell);
-        const u64 q = mc[gm].q, qi = mc[gm].qneg_inv;
-        U128 acc = {0, 0};
-#pragma unroll
-        for (int i = 0; i < NS; ++i) mac_wide(acc, y[i], sh[i * M + gm]);
-        const u64 r = redc(acc, q, qi);
-        dst[(size_t)t * n] = sub_mod(r, mul_shoup(v, __ldg(dm + gm), __ldg(dmp + gm), q), q);
-    }
+    for (int t = 0; t < lo; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + t * RL, y0, y1, v);
+    for (int t = hi; t < ell; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + t * RL, y0, y1, v);
+    for (int t = ell; t < next; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + (L + t - ell) * RL, y0, y1, v);
 }
 
 // Inner product with the switching key: acc_b[t] = sum_j E_j[t] k_{j,b}[t].
@@ -117,6 +149,7 @@ struct IpGroups {
 
 // BETA = number of digits at this level (compile-time, so the per-thread key
 // values stay in registers); BETA = 0 selects a generic loop for larger counts.
+// Products are summed carry-free (Acc30) and reduced by one REDC.
 template <int BETA>
 __global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *const *in,
                                             const u64 *ext, long long ext_stride, IpGroups groups, u64 *acc,
@@ -132,24 +165,31 @@ __global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, in
     // digit holding limb t (t < ell), -1 for special-prime limbs
     const int own = t < ell ? t / alpha : -1;
     if constexpr (BETA > 0) {
-        u64 k0[BETA], k1[BETA];
+        u64 k0[BETA], k1[BETA];   // key values, split
 #pragma unroll
         for (int j = 0; j < BETA; ++j) {
-            k0[j] = __ldg(gr.key + (((size_t)j * 2 + 0) * M + gm) * n + k);
-            k1[j] = __ldg(gr.key + (((size_t)j * 2 + 1) * M + gm) * n + k);
+            uint32_t a0, a1;
+            split30(__ldg(gr.key + (((size_t)j * 2 + 0) * M + gm) * n + k), a0, a1);
+            k0[j] = (u64)a0 | ((u64)a1 << 32);
+            split30(__ldg(gr.key + (((size_t)j * 2 + 1) * M + gm) * n + k), a0, a1);
+            k1[j] = (u64)a0 | ((u64)a1 << 32);
         }
         for (int it = gr.first; it < gr.first + gr.count; ++it) {
-            U128 a0 = {0, 0}, a1 = {0, 0};
+            Acc30 a0, a1;
+            acc30_zero(a0);
+            acc30_zero(a1);
             const u64 *e_it = ext + it * ext_stride + (size_t)t * n + k;
 #pragma unroll
             for (int j = 0; j < BETA; ++j) {
                 const u64 e = (j == own) ? in[it][(size_t)t * n + k] : e_it[(size_t)j * next * n];
-                mac_wide(a0, e, k0[j]);
-                mac_wide(a1, e, k1[j]);
+                uint32_t e0, e1;
+                split30(e, e0, e1);
+                acc30_mac(a0, e0, e1, k0[j]);
+                acc30_mac(a1, e0, e1, k1[j]);
             }
             u64 *o = acc + it * acc_stride;
-            o[(size_t)t * n + k] = redc(a0, m.q, m.qneg_inv);
-            o[((size_t)next + t) * n + k] = redc(a1, m.q, m.qneg_inv);
+            o[(size_t)t * n + k] = redc(acc30_value(a0), m.q, m.qneg_inv);
+            o[((size_t)next + t) * n + k] = redc(acc30_value(a1), m.q, m.qneg_inv);
         }
     } else {
         const int beta = (ell + alpha - 1) / alpha;
@@ -176,40 +216,45 @@ __global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, in
 // conv = sum_k y_k (P/p_k) - v P lies in [-P/2, P/2) and the final
 // (acc - conv) / P is acc / P rounded to nearest: a zero-mean error
 // (Halevi-Polyakov-Shoup floating-point correction, CT-RSA 2019).
+// One carry-free accumulation of KK + 1 products (the last v * (-P mod q_t))
+// and one REDC per output.
 // in = acc (coefficient rep. on the P limbs), out conv [items][2][ell][n].
 template <int KK>
-__global__ void __launch_bounds__(256) k_moddown_bconv(int ell, int L, int M, int n, const u64 *acc,
+__global__ void __launch_bounds__(256, 4) k_moddown_bconv(int ell, int L, int M, int n, const u64 *acc,
                                                        long long acc_stride, u64 *conv, const ModConst *__restrict__ mc,
                                                        const u64 *__restrict__ hinv, const u64 *__restrict__ hinvp,
-                                                       const u64 *__restrict__ hmont, const u64 *__restrict__ pmod,
-                                                       const u64 *__restrict__ pmodp, const double *__restrict__ inv_q)
+                                                       const u64 *__restrict__ hsplit, const u64 *__restrict__ negp,
+                                                       const double *__restrict__ inv_q)
 {
-    extern __shared__ u64 sh[];   // [KK][M]
-    for (int x = threadIdx.x; x < KK * M; x += blockDim.x) sh[x] = hmont[x];
+    constexpr int RL = bconv_row<KK>();
+    extern __shared__ __align__(16) u64 sh[];   // [ell][RL]
+    for (int x = threadIdx.x; x < ell * RL; x += blockDim.x) {
+        const int t = x / RL, c = x - t * RL;
+        u64 w = 0;
+        if (c < KK) w = hsplit[(size_t)c * M + t];
+        else if (c == KK) w = negp[t];
+        else if (c == KK + 1) w = mc[t].q;
+        else if (c == KK + 2) w = mc[t].qneg_inv;
+        sh[x] = w;
+    }
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int b = blockIdx.y, it = blockIdx.z;
     const int next = ell + KK;
     const u64 *src = acc + it * acc_stride + ((size_t)b * next + ell) * n;
-    u64 y[KK];
+    uint32_t y0[KK], y1[KK];
     double f = 0.0;
 #pragma unroll
     for (int i = 0; i < KK; ++i) {
         const u64 p = mc[L + i].q;
-        y[i] = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), p);
-        f = fma((double)y[i], __ldg(inv_q + L + i), f);
+        const u64 y = mul_shoup(src[(size_t)i * n + k], __ldg(hinv + i), __ldg(hinvp + i), p);
+        f = fma((double)y, __ldg(inv_q + L + i), f);
+        split30(y, y0[i], y1[i]);
     }
-    const u64 v = (u64)rint(f);
+    const uint32_t v = (uint32_t)rint(f);
     u64 *dst = conv + ((size_t)it * 2 + b) * ell * n + k;
-    for (int t = 0; t < ell; ++t) {
-        const u64 q = mc[t].q, qi = mc[t].qneg_inv;
-        U128 a = {0, 0};
-#pragma unroll
-        for (int i = 0; i < KK; ++i) mac_wide(a, y[i], sh[i * M + t]);
-        const u64 r = redc(a, q, qi);
-        dst[(size_t)t * n] = sub_mod(r, mul_shoup(v, __ldg(pmod + t), __ldg(pmodp + t), q), q);
-    }
+    for (int t = 0; t < ell; ++t) dst[(size_t)t * n] = bconv_out<KK>(sh + t * RL, y0, y1, v);
 }
 
 // out_b[i] = base_b[sigma(i)] + (acc_b[i] - conv_b[i]) P^{-1} mod q_i
@@ -565,14 +610,13 @@ void modup_bconv(Ctx &ctx, int items, int ell, const u64 *coef, long long coef_s
     const int full = ell / ctx.alpha;            // digits of width alpha
     const int last = ell - full * ctx.alpha;     // width of a truncated last digit (0: none)
     auto launch = [&](int digit0, int ndig, int ns) {
-        const size_t smem = (size_t)ns * ctx.M * sizeof(u64);
+        const size_t smem = (size_t)((ns + 4) & ~1) * ctx.M * sizeof(u64);
         const dim3 grid((ctx.n + kT - 1) / kT, ndig, items);
         cudaEvent_t t0_ = prof_begin(ctx);
         ns_dispatch(ns, [&](auto NS) {
             k_modup_bconv<decltype(NS)::value><<<grid, kT, smem, ctx.stream>>>(
                 digit0, ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, coef, coef_stride, ext, ext_stride, ctx.dt.mc,
-                ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_mont, ctx.dt.mu_dmod, ctx.dt.mu_dmod_p,
-                ctx.dt.inv_q);
+                ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_split, ctx.dt.mu_negd_split, ctx.dt.inv_q);
         });
         double macs = 0;
         for (int d = digit0; d < digit0 + ndig; ++d) macs += (double)ns * (ell + ctx.K - ns);
@@ -648,13 +692,13 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
             pm.mi[b * ctx.K + k] = ctx.L + k;
         }
     ntt_inverse(ctx, Batch{acc, acc_stride, items, nullptr}, pm);
-    const size_t smem = (size_t)ctx.K * ctx.M * sizeof(u64);
+    const size_t smem = (size_t)((ctx.K + 4) & ~1) * ell * sizeof(u64);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         ns_dispatch(ctx.K, [&](auto KK) {
             k_moddown_bconv<decltype(KK)::value><<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
                 ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv, ctx.dt.md_hat_inv_p,
-                ctx.dt.md_hat_mont, ctx.dt.md_pmod, ctx.dt.md_pmod_p, ctx.dt.inv_q);
+                ctx.dt.md_hat_split, ctx.dt.md_negp_split, ctx.dt.inv_q);
         });
         prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");
     }

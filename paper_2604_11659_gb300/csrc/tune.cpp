@@ -1,11 +1,18 @@
-// Rotation-plan base tuner: for a product's Alg. 1 plan, the number of key
+// Tuners.
+//
+// Rotation-plan base: for a product's Alg. 1 plan, the number of key
 // switches its rotations need depends on the base b of the rotation plan
 // (one key switch per nonzero base-b digit of each amount), and the key
 // memory on the number of keys (every d*b^t < S, 1 <= d < b).  The tuner
 // counts both for every power-of-two base and returns the base with the
 // fewest key switches whose keys fit the budget.
+//
+// NTT launch chunk: times the key-switching transforms of one match batch
+// (forward NTT of the ModUp extension, inverse NTT of the input limbs) on
+// scratch buffers for every candidate chunk and keeps the fastest.
 #include "engine.h"
 #include "handles.h"
+#include "kernels.h"
 
 namespace spfhe {
 
@@ -73,6 +80,75 @@ extern "C" spfhe_status spfhe_tune_rotation_base(uint32_t log_n, uint32_t L, uin
         *base = best;
         if (key_switches) *key_switches = best_ks;
         if (key_bytes) *key_bytes = best_bytes;
+        return SPFHE_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+extern "C" spfhe_status spfhe_tune_ntt_chunk(spfhe_ctx *ctx, uint32_t ell, uint32_t items, const uint32_t *candidates,
+                                            uint32_t n_candidates, uint32_t *best, double *ms)
+{
+    try {
+        if (!ctx || !candidates || !best || n_candidates == 0) throw Error(SPFHE_EINVAL, "null argument");
+        Ctx &c = ctx->c;
+        if (ell < 1 || (int)ell > c.L || items < 1 || items > 1024) throw Error(SPFHE_EINVAL, "bad shape");
+        const int beta = ((int)ell + c.alpha - 1) / c.alpha;
+        const int next = (int)ell + c.K;
+        const size_t ext_words = (size_t)items * beta * next * c.n;
+        const size_t in_words = (size_t)items * ell * c.n;
+        Scratch sc(c);
+        u64 *ext = sc.words(ext_words);
+        u64 *in = sc.words(in_words);
+        SPFHE_CHECK_CUDA(cudaMemsetAsync(ext, 0, ext_words * sizeof(u64), c.stream));
+        SPFHE_CHECK_CUDA(cudaMemsetAsync(in, 0, in_words * sizeof(u64), c.stream));
+        const LimbMap fm = modup_ntt_map(c, (int)ell);
+        const LimbMap im = limb_range(0, (int)ell, 0);
+        const Batch fb{ext, (long long)beta * next * c.n, (int)items, nullptr};
+        const Batch ib{in, (long long)ell * c.n, (int)items, nullptr};
+        const int saved = c.ntt_chunk;
+        const bool saved_ks = c.in_keyswitch;
+        c.in_keyswitch = true;
+        cudaEvent_t e0, e1;
+        SPFHE_CHECK_CUDA(cudaEventCreate(&e0));
+        SPFHE_CHECK_CUDA(cudaEventCreate(&e1));
+        float best_ms = 0;
+        uint32_t best_c = 0;
+        try {
+            for (uint32_t k = 0; k < n_candidates; ++k) {
+                if (candidates[k] > (1u << 20)) throw Error(SPFHE_EINVAL, "chunk out of range");
+                c.ntt_chunk = (int)candidates[k];
+                ntt_forward(c, fb, fm);   // warm-up
+                ntt_inverse(c, ib, im);
+                SPFHE_CHECK_CUDA(cudaEventRecord(e0, c.stream));
+                for (int r = 0; r < 3; ++r) {
+                    ntt_forward(c, fb, fm);
+                    ntt_inverse(c, ib, im);
+                }
+                SPFHE_CHECK_CUDA(cudaEventRecord(e1, c.stream));
+                SPFHE_CHECK_CUDA(cudaEventSynchronize(e1));
+                float t = 0;
+                SPFHE_CHECK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                t /= 3;
+                if (ms) ms[k] = t;
+                if (k == 0 || t < best_ms) {
+                    best_ms = t;
+                    best_c = candidates[k];
+                }
+            }
+        } catch (...) {
+            c.ntt_chunk = saved;
+            c.in_keyswitch = saved_ks;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.in_keyswitch = saved_ks;
+        c.ntt_chunk = (int)best_c;
+        *best = best_c;
         return SPFHE_OK;
     } catch (const Error &e) {
         set_last_error(e.what());

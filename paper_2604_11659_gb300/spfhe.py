@@ -62,6 +62,12 @@ _SIGS = [
     ("spfhe_sync", ctypes.c_int, [handle]),
     ("spfhe_launch_count", ctypes.c_uint64, [handle]),
     ("spfhe_ctx_set_match_batch", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_ctx_set_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_ctx_set_ntt_split", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_ctx_set_ntt_variant", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_tune_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_uint32), c_dblp]),
     ("spfhe_prof_enable", ctypes.c_int, [handle, ctypes.c_int]),
     ("spfhe_prof_read", ctypes.c_int, [handle, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), c_dblp, c_dblp, c_dblp]),
     ("spfhe_prof_classes", ctypes.c_int, []),
@@ -206,6 +212,27 @@ def spfhe_sync(ctx):
 
 def spfhe_ctx_set_match_batch(ctx, matches: int):
     _check(lib().spfhe_ctx_set_match_batch(ctx, int(matches)))
+
+
+def spfhe_ctx_set_ntt_chunk(ctx, limbs: int):
+    _check(lib().spfhe_ctx_set_ntt_chunk(ctx, int(limbs)))
+
+
+def spfhe_ctx_set_ntt_split(ctx, pass_a_stages: int):
+    _check(lib().spfhe_ctx_set_ntt_split(ctx, int(pass_a_stages)))
+
+
+def spfhe_ctx_set_ntt_variant(ctx, variant: int):
+    _check(lib().spfhe_ctx_set_ntt_variant(ctx, int(variant)))
+
+
+def spfhe_tune_ntt_chunk(ctx, ell: int, items: int, candidates):
+    """Time each candidate chunk, set the fastest; returns (best, ms list)."""
+    cand = (ctypes.c_uint32 * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_uint32()
+    _check(lib().spfhe_tune_ntt_chunk(ctx, int(ell), int(items), cand, len(candidates), ctypes.byref(best), ms))
+    return int(best.value), [float(x) for x in ms]
 
 
 def spfhe_launch_count(ctx) -> int:

@@ -34,14 +34,23 @@ def test_moduli_match_oracle(pair):
     assert [int(x) for x in psis] == pair.P.psis
 
 
-@pytest.mark.parametrize("log_n,q_bits", [(2, [60, 40, 40]), (4, [60, 40, 40]), (10, [60, 45, 45]),
-                                          (12, [60, 40, 40, 40]), (16, [60, 45, 45]), (17, [60, 50, 50])])
-def test_ntt_forward_inverse_bit_exact(log_n, q_bits):
+@pytest.mark.parametrize("log_n,q_bits,split", [(2, [60, 40, 40], 0), (4, [60, 40, 40], 0), (10, [60, 45, 45], 0),
+                                                (12, [60, 40, 40, 40], 0), (16, [60, 45, 45], 0),
+                                                (16, [60, 45, 59, 57], 7), (16, [60, 45, 45], 9),
+                                                (17, [60, 50, 50], 0), (17, [60, 50, 50], 9)])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_ntt_forward_inverse_bit_exact(log_n, q_bits, split, variant):
+    """Both butterfly paths (reduction-free below 2^58, bounded at and above),
+    every pass split and kernel variant, against the oracle's transform."""
     sp = need_gpu()
     import torch
+    if variant and log_n < 12:
+        pytest.skip("kernel variants apply to the two-pass radix-16 transform")
     recipe = synthetic.RingRecipe(log_n=log_n, q_bits=q_bits, dnum=1, scale_bits=40)
     p = Pair(recipe)
     try:
+        sp.spfhe_ctx_set_ntt_split(p.ctx, split)
+        sp.spfhe_ctx_set_ntt_variant(p.ctx, variant)
         n, M = p.n, p.M
         rng = np.random.default_rng(log_n)
         x = np.stack([rng.integers(0, m, n, dtype=np.uint64) for m in p.P.mods])
@@ -95,6 +104,36 @@ def test_keyswitch_at_every_level(pair):
         ha = pair.import_ct(a)
         h = pair.track("ct", pair.spfhe.spfhe_mult_relin(pair.ctx, pair.gkeys, ha, ha))
         pair.assert_ct_equal(h, want)
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 7, 64])
+def test_ntt_chunks_do_not_change_bits(pair, chunk):
+    """Cutting the transform batches into launch pairs of `chunk` limbs
+    (splitting items and limb maps) leaves every key switch bit-exact."""
+    o, P = pair.o, pair.P
+    rng = np.random.default_rng(11)
+    a = o.encrypt(o.encode(rng.uniform(-1, 1, P.slots), P.L, P.scale), pair.keys, rng)
+    want = o.mult_relin(a, a, pair.keys)
+    want_rot = o.rotate(a, 3, pair.keys)
+    sp = pair.spfhe
+    sp.spfhe_ctx_set_ntt_chunk(pair.ctx, chunk)
+    try:
+        ha = pair.import_ct(a)
+        pair.assert_ct_equal(pair.track("ct", sp.spfhe_mult_relin(pair.ctx, pair.gkeys, ha, ha)), want)
+        pair.assert_ct_equal(pair.track("ct", sp.spfhe_rotate(pair.ctx, pair.gkeys, ha, 3)), want_rot)
+    finally:
+        sp.spfhe_ctx_set_ntt_chunk(pair.ctx, 0)
+
+
+def test_ntt_chunk_tuner_picks_a_candidate(pair):
+    sp = pair.spfhe
+    cands = [0, 5, 64]
+    best, ms = sp.spfhe_tune_ntt_chunk(pair.ctx, pair.P.L - 1, 4, cands)
+    try:
+        assert best in cands and len(ms) == 3 and all(t > 0 for t in ms)
+        assert ms[cands.index(best)] == min(ms)
+    finally:
+        sp.spfhe_ctx_set_ntt_chunk(pair.ctx, 0)
 
 
 @pytest.mark.parametrize("r", [1, 3, 5, 17, -1, -7, 1000, 31])

@@ -2,15 +2,18 @@
 
 TEST INFRASTRUCTURE ONLY (tests/, __graft_entry__.smoke(), bench.py's
 cpu_baseline leg).  Follows the paper step by step; see oracle/ckks.py for the
-readings R1..R11 it relies on.
+readings R1..R11 it relies on.  spmspm_ct_ct_grouped is a reordering of
+Alg. 2 (lazy accumulation), not the paper's op order; it exists to check the
+library's variant of the same name.
 """
 from __future__ import annotations
 
+import ctypes
 from dataclasses import dataclass
 
 import numpy as np
 
-from .ckks import Ct, Keys, Oracle, Pt, rotation_plan
+from .ckks import Ct, Keys, Oracle, Pt, _p, addmod, lib, rotation_plan
 
 
 # ---------------------------------------------------------------------------
@@ -202,6 +205,156 @@ def spmspm_ct_ct(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list
         dot = orc.rotate(dot, rot_idx, keys)
         result[rc] = orc.add(result[rc], dot)
     return result
+
+
+# ---------------------------------------------------------------------------
+# lazy accumulation: a reordering of Alg. 2 (not the paper's op order)
+# ---------------------------------------------------------------------------
+def make_mask_grouped(orc: Oracle, slot: int, ell: int) -> Pt:
+    """One-hot plaintext e_slot at the operands' level ell, scale q_{ell-2}:
+    the mask of the lazy variant multiplies the unrescaled tensor product."""
+    return orc.encode_onehot(1.0, slot, ell, float(orc.mods[ell - 2]))
+
+
+def _rescale_polys(orc: Oracle, polys: list) -> list:
+    """Rescale (drop the top prime) of each polynomial, as orc.rescale does
+    for the two of a ciphertext."""
+    out = []
+    for d in polys:
+        c = np.ascontiguousarray(d.copy())
+        ell = c.shape[0]
+        lib().or_rescale(ctypes.byref(orc._cs), _p(c), ell)
+        out.append(c[: ell - 1].copy())
+    return out
+
+
+def group_key(mt: Match, S: int, cols: int) -> tuple:
+    """(result chunk, final rotation amount) of a match (reading R3/R4)."""
+    sa, sb = mt.a_pos % S, mt.b_pos % S
+    t = mt.i * cols + mt.j
+    return t // S, (min(sa, sb) - t % S) % S
+
+
+def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_cts: list,
+                         rows: int, cols: int, mask_pt: Pt | None = None, merge_digits: bool = True,
+                         counts: OpCounts | None = None) -> list:
+    """Lazy accumulation of Alg. 2's products.
+
+    Alignment rotations and the tensor product are Alg. 2's.  Then, instead
+    of relinearising, rescaling, masking and rotating every product:
+      1. each tensor product (three polynomials at the operands' level ell)
+         is multiplied by its mask e_{min_slot} (at level ell, scale
+         q_{ell-2}) and summed into the group of matches that share the
+         result chunk and the final rotation amount r;
+      2. per group: two rescales of the three polynomials (level ell-2), one
+         relinearisation (a key switch of the s^2 part), and a rotation by
+         the lowest base-b digit of r;
+      3. merge_digits: the rotated groups are summed per (chunk, remaining
+         amount) and every sum is rotated by its next digit, digit by digit,
+         until nothing remains; otherwise each group is rotated by the whole
+         of r (its rotation plan);
+      4. everything left for a result chunk is added into it.
+    Rotation and relinearisation are linear in the ciphertext, so the result
+    decrypts to the same product as Alg. 2 (within CKKS noise); the
+    ciphertext bits differ from Alg. 2's.  Result chunks: level ell-2, scale
+    scale_A scale_B / q_{ell-1}.  mask_pt: the slot-0 mask at level ell
+    (make_mask_grouped); the mask for slot p is its automorphism
+    X -> X^(5^-p)."""
+    P = orc.P
+    S = P.slots
+    b = P.rot_base
+    if counts is None:
+        counts = OpCounts()
+    ell = A_cts[0].level
+    nres = max(1, -(-(rows * cols) // S))
+    rscale = result_scale(orc, ell, A_cts[0].scale, B_cts[0].scale)
+    result = [orc.zero_ct(ell - 2, rscale) for _ in range(nres)]
+    matches = alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols)
+    if mask_pt is None:
+        mask_pt = make_mask_grouped(orc, 0, ell)
+    mods = orc.mods[:ell]
+    mi = np.arange(ell, dtype=np.int32)
+    rot_cache = {}
+
+    def rotated(which: str, chunk: int, amount: int) -> Ct:
+        key = (which, chunk, amount)
+        if key not in rot_cache:
+            src = (A_cts if which == "A" else B_cts)[chunk]
+            rot_cache[key] = orc.rotate(src, amount, keys)
+            counts.ks_align += len(rotation_plan(amount, S, P.rot_base))
+        return rot_cache[key]
+
+    groups = {}
+    for mt in matches:
+        counts.matches += 1
+        ca, sa = divmod(mt.a_pos, S)
+        cb, sb = divmod(mt.b_pos, S)
+        vA, vB = A_cts[ca], B_cts[cb]
+        min_slot = sa
+        if sa < sb:
+            vB = rotated("B", cb, sb - sa)
+        elif sb < sa:
+            vA = rotated("A", ca, sa - sb)
+            min_slot = sb
+        d0, d1, d2, _ = orc.tensor(vA, vB)
+        g = pow(pow(5, min_slot, 2 * P.n), -1, 2 * P.n)
+        m = np.stack([_automorph_limb(orc, mask_pt.m[i], g, q) for i, q in enumerate(mods)])
+        prod = [orc.rns_polymul(d, m, mi) for d in (d0, d1, d2)]
+        key = group_key(mt, S, cols)
+        if key in groups:
+            groups[key] = [np.stack([addmod(x[i], y[i], q) for i, q in enumerate(mods)])
+                           for x, y in zip(groups[key], prod)]
+        else:
+            groups[key] = prod
+
+    stage = {}
+    sc = A_cts[0].scale * B_cts[0].scale * mask_pt.scale / orc.mods[ell - 1] / orc.mods[ell - 2]
+    for key in sorted(groups):
+        rc, r = key
+        d = _rescale_polys(orc, _rescale_polys(orc, groups[key]))
+        counts.rescales += 2
+        ct = orc.relinearize(d[0], d[1], d[2], sc, keys)
+        counts.ks_relin += 1
+        step = r % b if merge_digits else r
+        if step:
+            counts.ks_final += len(rotation_plan(step, S, P.rot_base))
+            ct = orc.rotate(ct, step, keys)
+        nk = (rc, r - step)
+        stage[nk] = orc.add(stage[nk], ct) if nk in stage else ct
+    w = b
+    while any(rem for (_, rem) in stage):
+        nxt = {}
+        for (rc, rem) in sorted(stage):
+            ct = stage[(rc, rem)]
+            d = (rem // w) % b
+            if d:
+                ct = orc.rotate_single(ct, d * w, keys)
+                counts.ks_final += 1
+            nk = (rc, rem - d * w)
+            nxt[nk] = orc.add(nxt[nk], ct) if nk in nxt else ct
+        stage = nxt
+        w *= b
+    for (rc, _), ct in sorted(stage.items()):
+        result[rc] = orc.add(result[rc], ct)
+    return result
+
+
+def grouped_key_switches(A_csr, B_csc, rows: int, cols: int, slots: int, base: int, merge_digits: bool = True):
+    """(relinearisations, final-rotation key switches) of the lazy variant,
+    counted from the plan alone."""
+    groups = set()
+    for mt in alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols):
+        groups.add(group_key(mt, slots, cols))
+    if not merge_digits:
+        return len(groups), sum(len(rotation_plan(r, slots, base)) for _, r in groups)
+    ks = sum(1 for _, r in groups if r % base)
+    keys = {(rc, r - r % base) for rc, r in groups}
+    w = base
+    while any(rem for _, rem in keys):
+        ks += sum(1 for _, rem in keys if (rem // w) % base)
+        keys = {(rc, rem - ((rem // w) % base) * w) for rc, rem in keys}
+        w *= base
+    return len(groups), ks
 
 
 def _automorph_limb(orc: Oracle, a: np.ndarray, g: int, q: int) -> np.ndarray:

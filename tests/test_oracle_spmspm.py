@@ -74,6 +74,10 @@ def _run(case, rot_base=None, dnum=None, variant="ct_ct", seed=7):
     if variant == "ct_ct":
         B_cts = [o.encrypt(o.encode(z, P.L, P.scale), keys, rng) for z in spmspm.pack_values(Bd, P.slots)]
         res = spmspm.spmspm_ct_ct(o, keys, (Aip, Aix), A_cts, (Bip, Bix), B_cts, rows, cols, counts=counts)
+    elif variant.startswith("grouped"):
+        B_cts = [o.encrypt(o.encode(z, P.L, P.scale), keys, rng) for z in spmspm.pack_values(Bd, P.slots)]
+        res = spmspm.spmspm_ct_ct_grouped(o, keys, (Aip, Aix), A_cts, (Bip, Bix), B_cts, rows, cols,
+                                          merge_digits=variant == "grouped", counts=counts)
     else:
         res = spmspm.spmspm_ct_pt(o, keys, (Aip, Aix), A_cts, (Bip, Bix), Bd, rows, cols, counts=counts)
     C = spmspm.decrypt_result(o, keys, res, rows, cols)
@@ -134,3 +138,84 @@ def test_16x16_workload_matches_fp64():
     ref = spmspm.matmul_fp64(case.A, case.B)
     assert np.max(np.abs(C - ref)) < 1e-4
     assert spmspm.frobenius(C, ref) < 1e-3
+
+
+# ---- lazy accumulation (a reordering of Alg. 2, checked against FP64) -------
+def _dense_groups(A, B, S):
+    """(result chunk, final amount) -> match count, enumerated from the dense
+    matrices with slot positions taken from running nonzero counts."""
+    rows, inner = A.shape
+    cols = B.shape[1]
+    a_pos = np.cumsum((A != 0).ravel()).reshape(A.shape) - 1          # CSR order
+    b_pos = np.cumsum((B.T != 0).ravel()).reshape(B.T.shape) - 1      # CSC order
+    groups = {}
+    for i in range(rows):
+        for j in range(cols):
+            for k in range(inner):
+                if A[i, k] != 0 and B[k, j] != 0:
+                    t = i * cols + j
+                    r = (min(a_pos[i, k] % S, b_pos[j, k] % S) - t % S) % S
+                    key = (t // S, r)
+                    groups[key] = groups.get(key, 0) + 1
+    return groups
+
+
+def _tree_key_switches(groups, S, b):
+    """Digit-by-digit merge of the group amounts, simulated on the amounts."""
+    ks = 0
+    live = set()
+    for rc, r in groups:
+        if r % b:
+            ks += 1
+        live.add((rc, r - r % b))
+    w = b
+    while w < S:
+        nxt = set()
+        for rc, rem in live:
+            d = (rem // w) % b
+            ks += d != 0
+            nxt.add((rc, rem - d * w))
+        live = nxt
+        w *= b
+    return ks
+
+
+@pytest.mark.parametrize("seed,d,s,rot_base", [(0, 4, 0.5, 2), (1, 6, 0.3, 4), (2, 5, 0.0, 4), (3, 8, 0.5, 8)])
+def test_grouped_product_matches_fp64_and_counts(seed, d, s, rot_base):
+    case = synthetic.tiny_case(seed, d, s, log_n=6, rot_base=rot_base)
+    o, P, keys, res, C, counts, (Aip, Aix, Bip, Bix) = _run(case, rot_base=rot_base, variant="grouped")
+    ref = spmspm.matmul_fp64(case.A, case.B)
+    assert np.max(np.abs(C - ref)) < 1e-4
+    groups = _dense_groups(case.A, case.B, P.slots)
+    assert counts.matches == sum(groups.values())
+    assert counts.ks_relin == len(groups) and counts.rescales == 2 * len(groups)
+    assert counts.ks_final == _tree_key_switches(groups, P.slots, P.rot_base)
+    assert (counts.ks_relin, counts.ks_final) == spmspm.grouped_key_switches(
+        (Aip, Aix), (Bip, Bix), d, d, P.slots, P.rot_base)
+
+
+def test_grouped_merges_matches_and_saves_key_switches():
+    """A dense 8x8 product on 32 slots: many matches share (chunk, amount),
+    so the lazy variant needs fewer relinearisations and final-rotation key
+    switches than Alg. 2, with or without merging digits, and all three
+    decrypt to the FP64 product."""
+    case = synthetic.tiny_case(9, 8, 0.0, log_n=6, rot_base=4)
+    ref = spmspm.matmul_fp64(case.A, case.B)
+    _, _, _, _, C_lit, lit, _ = _run(case, rot_base=4)
+    _, _, _, res_g, C_g, grp, _ = _run(case, rot_base=4, variant="grouped")
+    _, _, _, _, C_n, nom, _ = _run(case, rot_base=4, variant="grouped_nomerge")
+    for C in (C_lit, C_g, C_n):
+        assert np.max(np.abs(C - ref)) < 1e-4
+    assert grp.matches == lit.matches == 512
+    assert grp.ks_relin < lit.ks_relin and grp.ks_relin == nom.ks_relin
+    assert grp.ks_final < nom.ks_final < lit.ks_final
+    assert grp.ks_align == lit.ks_align
+    assert len(res_g) == 2
+
+
+def test_grouped_fully_sparse_gives_exact_zero():
+    case = synthetic.tiny_case(6, 4, 1.0, log_n=6)
+    o, P, keys, res, C, counts, _ = _run(case, variant="grouped")
+    assert counts.matches == 0 and counts.ks_relin == 0
+    assert all(not r.c0.any() and not r.c1.any() for r in res)
+    assert np.array_equal(C, np.zeros((4, 4)))

@@ -305,6 +305,29 @@ spfhe_status spfhe_sparse_matmul_ct_pt(spfhe_ctx *ctx, const spfhe_keys *keys,
                                        spfhe_pt *const *B_pts, spfhe_ct **C_chunks, size_t n_c,
                                        spfhe_stats *stats);
 
+/* Lazy-accumulation variant of spfhe_sparse_matmul_ct_ct (a library
+ * extension that reorders Alg. 2; the paper has no counterpart).  Alignment
+ * rotations and tensor products are Alg. 2's; each tensor product is
+ * multiplied by its mask and summed into the group of matches sharing the
+ * result chunk and the final rotation amount r; each group is rescaled,
+ * relinearised (at level L-1), rescaled again and rotated, by the lowest
+ * base-b digit of r when
+ * merge_digits != 0 (the rotated groups are then summed per remaining amount
+ * and rotated digit by digit) or by the whole of r otherwise.  The result
+ * decrypts like Alg. 2's product (relinearisation and rotation are linear),
+ * with one relinearisation per group instead of per match and fewer
+ * final-rotation key switches; its ciphertext bits differ from Alg. 2's.
+ * Arguments as spfhe_sparse_matmul_ct_ct, except mask0: NULL or the slot-0
+ * one-hot plaintext at the operands' level L (not L-1), scale q_{L-2}.
+ * stats: ks_relin counts groups, rescales two per group.  Every distinct alignment rotation is held in device memory for
+ * the whole call: SPFHE_ENOMEM (before any launch) when it and the digit
+ * tree's accumulators do not fit.  Blocks until the result is ready. */
+spfhe_status spfhe_sparse_matmul_ct_ct_grouped(spfhe_ctx *ctx, const spfhe_keys *keys,
+                                               const spfhe_sparse_meta *A_csr, spfhe_ct *const *A_chunks, size_t n_a,
+                                               const spfhe_sparse_meta *B_csc, spfhe_ct *const *B_chunks, size_t n_b,
+                                               const spfhe_pt *mask0, int merge_digits, spfhe_ct **C_chunks,
+                                               size_t n_c, spfhe_stats *stats);
+
 /* NTT launch-chunk tuner (library extension; the paper has no tuner).  Times
  * the key-switching transforms of one match batch at level ell (forward NTT
  * of the ModUp extension of `items` polynomials, inverse NTT of their ell

@@ -246,9 +246,10 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
          is multiplied by its mask e_{min_slot} (at level ell, scale
          q_{ell-2}) and summed into the group of matches that share the
          result chunk and the final rotation amount r;
-      2. per group: two rescales of the three polynomials (level ell-2), one
-         relinearisation (a key switch of the s^2 part), and a rotation by
-         the lowest base-b digit of r;
+      2. per group: a rescale of the three polynomials (level ell-1), one
+         relinearisation (a key switch of the s^2 part) at level ell-1, a
+         rescale of the resulting ciphertext (level ell-2), and a rotation
+         by the lowest base-b digit of r;
       3. merge_digits: the rotated groups are summed per (chunk, remaining
          amount) and every sum is rotated by its next digit, digit by digit,
          until nothing remains; otherwise each group is rotated by the whole
@@ -308,12 +309,15 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
             groups[key] = prod
 
     stage = {}
-    sc = A_cts[0].scale * B_cts[0].scale * mask_pt.scale / orc.mods[ell - 1] / orc.mods[ell - 2]
+    sc = A_cts[0].scale * B_cts[0].scale * mask_pt.scale / orc.mods[ell - 1]
     for key in sorted(groups):
         rc, r = key
-        d = _rescale_polys(orc, _rescale_polys(orc, groups[key]))
-        counts.rescales += 2
+        # relinearise between the rescales: the rounding of the first rescale
+        # on the s^2 part is then divided by q_{ell-2} like everything else
+        d = _rescale_polys(orc, groups[key])
         ct = orc.relinearize(d[0], d[1], d[2], sc, keys)
+        ct = orc.rescale(ct)
+        counts.rescales += 2
         counts.ks_relin += 1
         step = r % b if merge_digits else r
         if step:

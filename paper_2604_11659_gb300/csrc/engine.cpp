@@ -61,6 +61,32 @@ const u64 *Engine::level_mask(int ell)
     return m;
 }
 
+int check_ct_ct(const Ctx &ctx, const spfhe_sparse_meta &A, const std::vector<Ct *> &Ach,
+                const spfhe_sparse_meta &B, const std::vector<Ct *> &Bch, size_t n_c, double *rscale)
+{
+    const int S = ctx.S;
+    validate_pair(A, B);
+    if (Ach.empty() || Bch.empty()) throw Error(SPFHE_EINVAL, "no operand chunks");
+    if (Ach.size() != chunks_for(A.nnz, S) || Bch.size() != chunks_for(B.nnz, S))
+        throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
+    if (n_c != chunks_for((long long)A.rows * B.cols, S))
+        throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
+    const int ell = Ach[0] ? Ach[0]->level : 0;
+    for (Ct *c : Ach)
+        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "A chunks must share one level");
+    for (Ct *c : Bch)
+        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "B chunks must share A's level");
+    if (ell < 3) throw Error(SPFHE_ELEVEL, "ct x ct needs operands at level >= 3");
+    const double sa = Ach[0]->scale, sb = Bch[0]->scale;
+    for (Ct *c : Ach)
+        if (std::fabs(c->scale - sa) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A chunk scales differ");
+    for (Ct *c : Bch)
+        if (std::fabs(c->scale - sb) > 1e-9 * sb) throw Error(SPFHE_ESCALE, "B chunk scales differ");
+    if (std::fabs(sa - sb) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A and B scales differ");
+    *rscale = sa * sb / (double)ctx.mods[ell - 1];
+    return ell;
+}
+
 void Engine::add(Job *job)
 {
     Ctx &ctx = ctx_;
@@ -70,27 +96,9 @@ void Engine::add(Job *job)
     job->A.indices = job->aix.empty() ? nullptr : job->aix.data();
     job->B.indptr = job->bip.data();
     job->B.indices = job->bix.empty() ? nullptr : job->bix.data();
-    validate_pair(job->A, job->B);
     if (!job->keys) throw Error(SPFHE_EINVAL, "null keys");
-    if (job->Ach.empty() || job->Bch.empty()) throw Error(SPFHE_EINVAL, "no operand chunks");
-    if (job->Ach.size() != chunks_for(job->A.nnz, S) || job->Bch.size() != chunks_for(job->B.nnz, S))
-        throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
-    if (job->n_c != chunks_for((long long)job->A.rows * job->B.cols, S))
-        throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
-    const int ell = job->Ach[0] ? job->Ach[0]->level : 0;
-    for (Ct *c : job->Ach)
-        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "A chunks must share one level");
-    for (Ct *c : job->Bch)
-        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "B chunks must share A's level");
-    if (ell < 3) throw Error(SPFHE_ELEVEL, "ct x ct needs operands at level >= 3");
-    const double sa = job->Ach[0]->scale, sb = job->Bch[0]->scale;
-    for (Ct *c : job->Ach)
-        if (std::fabs(c->scale - sa) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A chunk scales differ");
-    for (Ct *c : job->Bch)
-        if (std::fabs(c->scale - sb) > 1e-9 * sb) throw Error(SPFHE_ESCALE, "B chunk scales differ");
-    if (std::fabs(sa - sb) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A and B scales differ");
+    const int ell = check_ct_ct(ctx, job->A, job->Ach, job->B, job->Bch, job->n_c, &job->rscale);
     job->ell = ell;
-    job->rscale = sa * sb / (double)ctx.mods[ell - 1];
     job->id = next_id_++;
 
     const std::vector<MatchRec> ms = plan_alg1(job->A, job->B);

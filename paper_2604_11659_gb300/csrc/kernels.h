@@ -53,13 +53,20 @@ void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const 
 void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv,
              const u64 *const *base, const int *base_g, bool base_c1, u64 *out, long long out_stride);
 
-// Rescale every item [2][ell][n] -> out [2][ell-1][n].
-void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride);
+// Rescale every item [polys][ell][n] -> out [polys][ell-1][n] (polys 1..3);
+// tmp holds items * polys * ell * n words.
+void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride,
+             int polys = 2);
 
-// ct[item] (= [2][ell][n]) *= mask permuted by sigma_{g[item]}; mask [ell][n]
-// in Montgomery form.
+// ct[item] (= [polys][ell][n]) *= mask permuted by sigma_{g[item]}; mask
+// [ell][n] in Montgomery form.
 void mul_plain_perm(Ctx &ctx, int items, int ell, u64 *ct, long long stride, const u64 *const *mask,
-                    const int *g);
+                    const int *g, int polys = 2);
+
+// Segmented sums over items of `polys` x ell limbs: tgt[g] (+)= sum of
+// src[seg[g]] .. src[seg[g+1]-1]; `into` adds to tgt's own value.
+void accumulate_seg(Ctx &ctx, int polys, int ell, int targets, u64 *const *tgt, const u64 *const *src,
+                    const int *seg, int sources, bool into);
 
 // result[2][ell][n] += sum over the listed items of x[item]
 void accumulate(Ctx &ctx, int ell, u64 *result, const u64 *x, long long stride, const int *ids, int count);

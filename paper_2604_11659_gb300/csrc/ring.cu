@@ -281,26 +281,26 @@ __global__ void k_moddown_final(int ell, int K, int log_n, const u64 *acc, long 
     out[it * out_stride + ((size_t)b * ell + i) * n + k] = v;
 }
 
-// Rescale, step 1: r = centred top limb (coefficient rep., [items][2][n]),
-// spread into tmp [items][2][ell-1][n] as [r]_{q_i}.
-__global__ void k_rescale_spread(int ell, int n, const u64 *top, u64 *tmp, const ModConst *__restrict__ mc,
+// Rescale, step 1: r = centred top limb (coefficient rep., [items][polys][n]),
+// spread into tmp [items][polys][ell-1][n] as [r]_{q_i}.
+__global__ void k_rescale_spread(int polys, int ell, int n, const u64 *top, u64 *tmp, const ModConst *__restrict__ mc,
                                  const u64 *__restrict__ qt_mod)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int bi = blockIdx.y, it = blockIdx.z;   // over 2 * (ell-1)
+    const int bi = blockIdx.y, it = blockIdx.z;   // over polys * (ell-1)
     const int b = bi / (ell - 1), i = bi % (ell - 1);
     const u64 qt = mc[ell - 1].q;
-    const u64 c = top[((size_t)it * 2 + b) * n + k];
+    const u64 c = top[((size_t)it * polys + b) * n + k];
     const ModConst m = mc[i];
     // c mod q_i: REDC(c) = c 2^-64, then times 2^64 mod q_i
     u64 r = mul_shoup(redc(U128{c, 0}, m.q, m.qneg_inv), m.r_mod, m.r_mod_p, m.q);
     if (c > (qt >> 1)) r = sub_mod(r, __ldg(qt_mod + i), m.q);   // r = c - q_t (negative representative)
-    tmp[(((size_t)it * 2 + b) * (ell - 1) + i) * n + k] = r;
+    tmp[(((size_t)it * polys + b) * (ell - 1) + i) * n + k] = r;
 }
 
-__global__ void k_rescale_final(int ell, int n, const u64 *const *in, const u64 *tmp, u64 *out, long long out_stride,
-                                const ModConst *__restrict__ mc, const u64 *__restrict__ inv,
+__global__ void k_rescale_final(int polys, int ell, int n, const u64 *const *in, const u64 *tmp, u64 *out,
+                                long long out_stride, const ModConst *__restrict__ mc, const u64 *__restrict__ inv,
                                 const u64 *__restrict__ invp)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,16 +309,16 @@ __global__ void k_rescale_final(int ell, int n, const u64 *const *in, const u64 
     const int b = bi / (ell - 1), i = bi % (ell - 1);
     const u64 q = mc[i].q;
     const u64 c = in[it][((size_t)b * ell + i) * n + k];
-    const u64 r = tmp[(((size_t)it * 2 + b) * (ell - 1) + i) * n + k];
+    const u64 r = tmp[(((size_t)it * polys + b) * (ell - 1) + i) * n + k];
     out[it * out_stride + ((size_t)b * (ell - 1) + i) * n + k] = mul_shoup(sub_mod(c, r, q), __ldg(inv + i), __ldg(invp + i), q);
 }
 
-__global__ void k_copy_top(int ell, int n, const u64 *const *in, u64 *top)
+__global__ void k_copy_top(int polys, int ell, int n, const u64 *const *in, u64 *top)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int b = blockIdx.y, it = blockIdx.z;
-    top[((size_t)it * 2 + b) * n + k] = in[it][((size_t)b * ell + ell - 1) * n + k];
+    top[((size_t)it * polys + b) * n + k] = in[it][((size_t)b * ell + ell - 1) * n + k];
 }
 
 __global__ void k_mul_plain_perm(int ell, int log_n, u64 *ct, long long stride, const u64 *const *mask, const int *g,
@@ -347,6 +347,22 @@ __global__ void k_accumulate(int ell, int n, u64 *res, const u64 *x, long long s
     u64 acc = res[off];
     for (int c = 0; c < count; ++c) acc = add_mod(acc, x[(long long)ids[c] * stride + off], q);
     res[off] = acc;
+}
+
+// Segmented sums: target g (blockIdx.z) receives the sum over its segment
+// [seg[g], seg[g+1]) of source items, plus its own value when `into`; each
+// item is `limbs` limbs (polynomials x ell), limb l has modulus l % ell.
+__global__ void k_accumulate_seg(int limbs, int ell, int n, u64 *const *tgt, const u64 *const *src, const int *seg,
+                                 int into, const ModConst *__restrict__ mc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int l = blockIdx.y, g = blockIdx.z;
+    const u64 q = mc[l % ell].q;
+    const size_t off = (size_t)l * n + k;
+    u64 acc = into ? tgt[g][off] : 0;
+    for (int c = seg[g]; c < seg[g + 1]; ++c) acc = add_mod(acc, src[c][off], q);
+    tgt[g][off] = acc;
 }
 
 __global__ void k_add(int polys, int ell, int n, const u64 *a, const u64 *b, u64 *out, const ModConst *__restrict__ mc)
@@ -719,54 +735,69 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
     }
 }
 
-void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride)
+void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride, int polys)
 {
     if (ell < 2) throw Error(SPFHE_ELEVEL, "rescale needs two limbs");
+    if (polys < 1 || polys > 3) throw Error(SPFHE_EINVAL, "rescale of 1 to 3 polynomials per item");
     const int n = ctx.n;
-    // tmp layout: [items][2][n] top limbs, then [items][2][ell-1][n]
+    // tmp layout: [items][polys][n] top limbs, then [items][polys][ell-1][n]
     u64 *top = tmp;
-    u64 *spread = tmp + (size_t)items * 2 * n;
+    u64 *spread = tmp + (size_t)items * polys * n;
     {
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_copy_top<<<grid_n(n, 2, items), kT, 0, ctx.stream>>>(ell, n, in, top);
-        prof_end(ctx, t0_, K_RESCALE, 32.0 * n * items, 0.0, "rescale copy");
+        k_copy_top<<<grid_n(n, polys, items), kT, 0, ctx.stream>>>(polys, ell, n, in, top);
+        prof_end(ctx, t0_, K_RESCALE, 16.0 * n * items * polys, 0.0, "rescale copy");
     }
     LimbMap tm;
-    tm.nl = 2;
-    tm.off[0] = 0;
-    tm.off[1] = 1;
-    tm.mi[0] = tm.mi[1] = ell - 1;
-    ntt_inverse(ctx, Batch{top, 2LL * n, items, nullptr}, tm);
+    tm.nl = polys;
+    for (int b = 0; b < polys; ++b) {
+        tm.off[b] = b;
+        tm.mi[b] = ell - 1;
+    }
+    ntt_inverse(ctx, Batch{top, (long long)polys * n, items, nullptr}, tm);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_rescale_spread<<<grid_n(n, 2 * (ell - 1), items), kT, 0, ctx.stream>>>(
-            ell, n, top, spread, ctx.dt.mc, ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L);
-        prof_end(ctx, t0_, K_RESCALE, 8.0 * n * items * (2.0 + 2.0 * (ell - 1)), 2.0 * n * items * (ell - 1), "rescale spread");
+        k_rescale_spread<<<grid_n(n, polys * (ell - 1), items), kT, 0, ctx.stream>>>(
+            polys, ell, n, top, spread, ctx.dt.mc, ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L);
+        prof_end(ctx, t0_, K_RESCALE, 8.0 * n * items * polys * ell, 1.0 * n * items * polys * (ell - 1), "rescale spread");
     }
     LimbMap sm;
-    sm.nl = 2 * (ell - 1);
-    for (int b = 0; b < 2; ++b)
+    sm.nl = polys * (ell - 1);
+    for (int b = 0; b < polys; ++b)
         for (int i = 0; i < ell - 1; ++i) {
             sm.off[b * (ell - 1) + i] = b * (ell - 1) + i;
             sm.mi[b * (ell - 1) + i] = i;
         }
-    ntt_forward(ctx, Batch{spread, 2LL * (ell - 1) * n, items, nullptr}, sm);
+    ntt_forward(ctx, Batch{spread, (long long)polys * (ell - 1) * n, items, nullptr}, sm);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_rescale_final<<<grid_n(n, 2 * (ell - 1), items), kT, 0, ctx.stream>>>(
-            ell, n, in, spread, out, out_stride, ctx.dt.mc, ctx.dt.rs_inv + (size_t)(ell - 1) * ctx.L,
+        k_rescale_final<<<grid_n(n, polys * (ell - 1), items), kT, 0, ctx.stream>>>(
+            polys, ell, n, in, spread, out, out_stride, ctx.dt.mc, ctx.dt.rs_inv + (size_t)(ell - 1) * ctx.L,
             ctx.dt.rs_inv_p + (size_t)(ell - 1) * ctx.L);
-        prof_end(ctx, t0_, K_RESCALE, 48.0 * n * items * (ell - 1), 2.0 * n * items * (ell - 1), "rescale final");
+        prof_end(ctx, t0_, K_RESCALE, 24.0 * n * items * polys * (ell - 1), 1.0 * n * items * polys * (ell - 1), "rescale final");
     }
 }
 
-void mul_plain_perm(Ctx &ctx, int items, int ell, u64 *ct, long long stride, const u64 *const *mask, const int *g)
+void mul_plain_perm(Ctx &ctx, int items, int ell, u64 *ct, long long stride, const u64 *const *mask, const int *g,
+                    int polys)
 {
     {
         cudaEvent_t t0_ = prof_begin(ctx);
-        k_mul_plain_perm<<<grid_n(ctx.n, 2 * ell, items), kT, 0, ctx.stream>>>(ell, ctx.log_n, ct, stride, mask, g,
-                                                                              ctx.dt.mc);
-        prof_end(ctx, t0_, K_MASK, 8.0 * ctx.n * (4.0 * items * ell + ell), 2.0 * ctx.n * items * ell, "mask multiply");
+        k_mul_plain_perm<<<grid_n(ctx.n, polys * ell, items), kT, 0, ctx.stream>>>(ell, ctx.log_n, ct, stride, mask,
+                                                                                  g, ctx.dt.mc);
+        prof_end(ctx, t0_, K_MASK, 8.0 * ctx.n * (2.0 * polys * items * ell + ell), 1.0 * ctx.n * polys * items * ell, "mask multiply");
+    }
+}
+
+void accumulate_seg(Ctx &ctx, int polys, int ell, int targets, u64 *const *tgt, const u64 *const *src,
+                    const int *seg, int sources, bool into)
+{
+    if (targets <= 0) return;
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_accumulate_seg<<<grid_n(ctx.n, polys * ell, targets), kT, 0, ctx.stream>>>(polys * ell, ell, ctx.n, tgt, src,
+                                                                                   seg, into ? 1 : 0, ctx.dt.mc);
+        prof_end(ctx, t0_, K_ACCUM, 8.0 * ctx.n * polys * ell * (sources + (into ? 2.0 : 1.0) * targets), 1.0 * ctx.n * polys * ell * sources, "segmented accumulate");
     }
 }
 

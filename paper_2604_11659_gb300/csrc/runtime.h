@@ -47,6 +47,7 @@ enum WsSlot {
     WS_MASK,
     WS_PTS,
     WS_MISC,
+    WS_GRP_SUM,
 };
 
 // ---- batched evaluator (ckks.cpp) ----

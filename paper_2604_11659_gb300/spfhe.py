@@ -109,6 +109,10 @@ _SIGS = [
                                                  ctypes.c_size_t, ctypes.POINTER(SparseMeta), c_dblp,
                                                  ctypes.POINTER(handle), ctypes.POINTER(handle), ctypes.c_size_t,
                                                  ctypes.POINTER(Stats)]),
+    ("spfhe_sparse_matmul_ct_ct_grouped", ctypes.c_int,
+     [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
+      ctypes.POINTER(handle), ctypes.c_size_t, handle, ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t,
+      ctypes.POINTER(Stats)]),
 ]
 
 class MatmulReq(ctypes.Structure):
@@ -439,6 +443,16 @@ def spfhe_sparse_matmul_ct_ct(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta,
     _check(lib().spfhe_sparse_matmul_ct_ct(ctx, keys, ctypes.byref(A), _handles(A_chunks), len(A_chunks),
                                            ctypes.byref(B), _handles(B_chunks), len(B_chunks), mask0, outs, n_c,
                                            ctypes.byref(st)))
+    return [handle(outs[i]) for i in range(n_c)], st.as_dict()
+
+
+def spfhe_sparse_matmul_ct_ct_grouped(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta, B_chunks, mask0, n_c: int,
+                                      merge_digits: bool = True):
+    outs = (handle * n_c)()
+    st = Stats()
+    _check(lib().spfhe_sparse_matmul_ct_ct_grouped(ctx, keys, ctypes.byref(A), _handles(A_chunks), len(A_chunks),
+                                                   ctypes.byref(B), _handles(B_chunks), len(B_chunks), mask0,
+                                                   1 if merge_digits else 0, outs, n_c, ctypes.byref(st)))
     return [handle(outs[i]) for i in range(n_c)], st.as_dict()
 
 

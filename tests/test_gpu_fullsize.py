@@ -56,15 +56,24 @@ def test_bench_ring_bit_exact_few_matches():
 
 def test_bench_workload_decrypts_within_tolerance():
     """The 128x128, 90 %-sparse product of the benchmark with the library's
-    own keys, encryption and masks: max |decrypt(C) - A B| < 1e-4."""
+    own keys, encryption and masks: max |decrypt(C) - A B| < 1e-4, for Alg. 2
+    as printed and for the lazy-accumulation variant, whose relinearisation
+    and final-rotation key switches equal the plan's group counts."""
     import torch
     import bench
     case = synthetic.case_128x128(seed=1)
     g = bench.GpuMatmul(case, 256, torch.cuda.current_stream().cuda_stream)
     try:
         outs, st = g.step()
-        assert st["matches"] == int(sum(np.count_nonzero(case.A[:, k]) * np.count_nonzero(case.B[k, :])
-                                        for k in range(128)))
+        want_matches = int(sum(np.count_nonzero(case.A[:, k]) * np.count_nonzero(case.B[k, :]) for k in range(128)))
+        assert st["matches"] == want_matches
+        err = g.check(outs)
+        g.free(outs)
+        assert err < 1e-4
+        outs, st = g.step(grouped=True)
+        Acsr, Bcsc = spmspm.dense_to_csr(case.A), spmspm.dense_to_csc(case.B)
+        relin, final = spmspm.grouped_key_switches(Acsr[:2], Bcsc[:2], 128, 128, 1 << 15, 256)
+        assert st["matches"] == want_matches and st["ks_relin"] == relin and st["ks_final"] == final
         err = g.check(outs)
         g.free(outs)
         assert err < 1e-4

@@ -30,6 +30,14 @@ sys.path.insert(0, ROOT)
 METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); keyswitch HBM GB/s; p99"
 ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", "moddown_bconv"}
 
+# DRAM bytes (read + write) per limb of one pass, from ncu captures of the
+# radix-16 kernels on the profiler case (bench.py --small-case: n = 2^16,
+# 288 limbs per launch, one launch each of pass A and pass B); the transform
+# classes' traffic per launch is this times the launch's limbs (assumes the
+# traffic grows in proportion to the limbs).
+NTT_DRAM_BYTES_PER_LIMB = {"ks_ntt_fwd": (239.771e6 / 288 + 287.337e6 / 288) / 2,
+                           "ntt_fwd": (239.771e6 / 288 + 287.337e6 / 288) / 2}
+
 
 def load_peaks():
     try:
@@ -677,7 +685,9 @@ def main():
         peak = alu_peak_mulmods(sm_max)
         achieved = dd["work"] / (dd["ms"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "Tmulmod/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tmulmod/s", "frac": achieved / peak,
+                "traffic": (NTT_DRAM_BYTES_PER_LIMB[dom] * dd["bytes"] / max(1, dd["launches"]) / (16.0 * g.n)
+                            if dom in NTT_DRAM_BYTES_PER_LIMB else None),
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
                 "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
                 "work_per_launch": dd["work"] / max(1, dd["launches"]),

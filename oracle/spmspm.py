@@ -308,10 +308,9 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
         else:
             groups[key] = prod
 
-    stage = {}
     sc = A_cts[0].scale * B_cts[0].scale * mask_pt.scale / orc.mods[ell - 1]
+    done = []
     for key in sorted(groups):
-        rc, r = key
         # relinearise between the rescales: the rounding of the first rescale
         # on the s^2 part is then divided by q_{ell-2} like everything else
         d = _rescale_polys(orc, groups[key])
@@ -319,6 +318,20 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
         ct = orc.rescale(ct)
         counts.rescales += 2
         counts.ks_relin += 1
+        done.append((key, ct))
+    _rotation_tree(orc, keys, done, result, merge_digits, counts)
+    return result
+
+
+def _rotation_tree(orc: Oracle, keys: Keys, items: list, result: list, merge_digits: bool, counts: OpCounts):
+    """Rotate every ((chunk, r), ct) of `items` left by r and add it into
+    result[chunk].  merge_digits: rotate by the lowest base-b digit of r, sum
+    per (chunk, remaining amount), then rotate each sum by its next digit,
+    digit by digit; otherwise rotate each item by r through its plan."""
+    P = orc.P
+    S, b = P.slots, P.rot_base
+    stage = {}
+    for (rc, r), ct in items:
         step = r % b if merge_digits else r
         if step:
             counts.ks_final += len(rotation_plan(step, S, P.rot_base))
@@ -340,6 +353,49 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
         w *= b
     for (rc, _), ct in sorted(stage.items()):
         result[rc] = orc.add(result[rc], ct)
+
+
+def spmspm_ct_pt_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_data: np.ndarray,
+                         rows: int, cols: int, b_pts: list | None = None, merge_digits: bool = True,
+                         counts: OpCounts | None = None) -> list:
+    """Lazy accumulation of the ct x pt products (reading R9): the weight
+    plaintexts B[k, j] e_{a_slot} of the matches sharing the result chunk and
+    the final rotation amount r = a_slot - t are summed per A chunk, each sum
+    multiplies its A chunk, the products of a group are added, rescaled once
+    and rotated through _rotation_tree.  Result at level L-1, scale Delta."""
+    P = orc.P
+    S = P.slots
+    if counts is None:
+        counts = OpCounts()
+    nres = max(1, -(-(rows * cols) // S))
+    result = [orc.zero_ct(P.L - 1, P.scale) for _ in range(nres)]
+    mods = orc.mods[: P.L]
+    sums = {}
+    for mt in alg1_matches(A_csr[0], A_csr[1], B_csc[0], B_csc[1], rows, cols):
+        counts.matches += 1
+        ca, sa = divmod(mt.a_pos, S)
+        if b_pts is None:
+            pt = orc.encode_onehot(float(B_data[mt.b_pos]), sa, P.L, weight_scale(orc))
+        else:
+            g = pow(pow(5, sa, 2 * P.n), -1, 2 * P.n)
+            base = b_pts[mt.b_pos]
+            pt = Pt(np.stack([_automorph_limb(orc, base.m[i], g, q) for i, q in enumerate(mods)]), base.scale)
+        t = mt.i * cols + mt.j
+        key = (t // S, (sa - t % S) % S)
+        sk = (key, ca)
+        if sk in sums:
+            sums[sk] = Pt(np.stack([addmod(sums[sk].m[i], pt.m[i], q) for i, q in enumerate(mods)]), pt.scale)
+        else:
+            sums[sk] = pt
+    groups = {}
+    for (key, ca) in sorted(sums):
+        prod = orc.mul_plain(A_cts[ca], sums[(key, ca)])
+        groups[key] = orc.add(groups[key], prod) if key in groups else prod
+    done = []
+    for key in sorted(groups):
+        done.append((key, orc.rescale(groups[key])))
+        counts.rescales += 1
+    _rotation_tree(orc, keys, done, result, merge_digits, counts)
     return result
 
 

@@ -78,6 +78,9 @@ def _run(case, rot_base=None, dnum=None, variant="ct_ct", seed=7):
         B_cts = [o.encrypt(o.encode(z, P.L, P.scale), keys, rng) for z in spmspm.pack_values(Bd, P.slots)]
         res = spmspm.spmspm_ct_ct_grouped(o, keys, (Aip, Aix), A_cts, (Bip, Bix), B_cts, rows, cols,
                                           merge_digits=variant == "grouped", counts=counts)
+    elif variant.startswith("ptgrouped"):
+        res = spmspm.spmspm_ct_pt_grouped(o, keys, (Aip, Aix), A_cts, (Bip, Bix), Bd, rows, cols,
+                                          merge_digits=variant == "ptgrouped", counts=counts)
     else:
         res = spmspm.spmspm_ct_pt(o, keys, (Aip, Aix), A_cts, (Bip, Bix), Bd, rows, cols, counts=counts)
     C = spmspm.decrypt_result(o, keys, res, rows, cols)
@@ -219,3 +222,33 @@ def test_grouped_fully_sparse_gives_exact_zero():
     assert counts.matches == 0 and counts.ks_relin == 0
     assert all(not r.c0.any() and not r.c1.any() for r in res)
     assert np.array_equal(C, np.zeros((4, 4)))
+
+
+def _dense_groups_pt(A, B, S):
+    """ct x pt groups: (result chunk, a_slot - t) -> match count."""
+    rows, inner = A.shape
+    cols = B.shape[1]
+    a_pos = np.cumsum((A != 0).ravel()).reshape(A.shape) - 1
+    groups = {}
+    for i in range(rows):
+        for j in range(cols):
+            for k in range(inner):
+                if A[i, k] != 0 and B[k, j] != 0:
+                    t = i * cols + j
+                    key = (t // S, (a_pos[i, k] % S - t % S) % S)
+                    groups[key] = groups.get(key, 0) + 1
+    return groups
+
+
+@pytest.mark.parametrize("seed,rows,inner,cols,s,rot_base", [(5, 3, 7, 5, 0.5, 2), (6, 8, 8, 8, 0.2, 4),
+                                                             (7, 6, 9, 4, 0.0, 8)])
+def test_ct_pt_grouped_matches_fp64_and_counts(seed, rows, inner, cols, s, rot_base):
+    case = synthetic.tiny_case(seed, 0, s, log_n=6, rows=rows, inner=inner, cols=cols, rot_base=rot_base)
+    o, P, keys, res, C, counts, _ = _run(case, rot_base=rot_base, variant="ptgrouped")
+    assert np.max(np.abs(C - spmspm.matmul_fp64(case.A, case.B))) < 1e-4
+    groups = _dense_groups_pt(case.A, case.B, P.slots)
+    assert counts.matches == sum(groups.values()) and counts.rescales == len(groups)
+    assert counts.ks_final == _tree_key_switches(groups, P.slots, P.rot_base)
+    _, _, _, _, C_n, nom, _ = _run(case, rot_base=rot_base, variant="ptgrouped_nomerge")
+    assert np.max(np.abs(C_n - spmspm.matmul_fp64(case.A, case.B))) < 1e-4
+    assert nom.ks_final >= counts.ks_final

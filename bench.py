@@ -325,11 +325,71 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
             "speedup_over_per_product_batching": res["per_product"] / res["batched"]}
 
 
+def dense_layer_pt(stream, rot_base=16):
+    """The pruned dense layer at the paper's sizing (N=2^17, L=35, dnum=5,
+    K=6): encrypted 64x784 ReLU-like activations times plaintext 784x128
+    N(0, 0.05^2) weights pruned to 90 %, through the lazy-accumulation ct x pt
+    product with the library's own weight encoding; one cold call (its
+    workspaces are allocated inside it), timed with CUDA events."""
+    import torch
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    case = synthetic.case_dense_layer(seed=3)
+    rec = case.ring
+    gp = gparams.ctx_params(rec, rot_base=rot_base)
+    ctx = sp.spfhe_ctx_create(gp, stream)
+    t0 = time.time()
+    keys = sp.spfhe_keygen(ctx, 31)
+    keygen_s = time.time() - t0
+    S = (1 << rec.log_n) // 2
+    Aip, Aix, Ad = to_csr(case.A)
+    Bip, Bix, Bd = to_csr(case.B.T)
+    Am = sp.sparse_meta(Aip, Aix, case.A.shape[0], case.A.shape[1])
+    Bm = sp.sparse_meta(Bip, Bix, case.B.shape[0], case.B.shape[1])
+    A_cts = []
+    for c in range(max(1, -(-len(Ad) // S))):
+        z = np.zeros(S)
+        part = Ad[c * S:(c + 1) * S]
+        z[: len(part)] = part
+        pt = sp.spfhe_encode(ctx, z, rec.L, rec.scale)
+        A_cts.append(sp.spfhe_encrypt(ctx, keys, pt, 40 + c))
+        sp.spfhe_pt_free(pt)
+    n_c = max(1, -(-(case.A.shape[0] * case.B.shape[1]) // S))
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    outs, st = sp.spfhe_sparse_matmul_ct_pt_grouped(ctx, keys, Am, A_cts, Bm, Bd, None, n_c)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    vals = []
+    for h in outs:
+        pt = sp.spfhe_decrypt(ctx, keys, h)
+        vals.append(sp.spfhe_decode(ctx, pt, S).real)
+        sp.spfhe_pt_free(pt)
+        sp.spfhe_ct_free(h)
+    C = np.concatenate(vals)[: case.A.shape[0] * case.B.shape[1]].reshape(case.A.shape[0], case.B.shape[1])
+    err = float(np.max(np.abs(C - case.A @ case.B)))
+    for h in A_cts:
+        sp.spfhe_ct_free(h)
+    sp.spfhe_keys_free(keys)
+    sp.spfhe_ctx_destroy(ctx)
+    return {"workload": "64x784 ReLU-like (50 %% zeros) x 784x128 N(0, 0.05^2) pruned to 90 %%, N=2^17, L=35, "
+                        "dnum=5, K=%d, rotation base %d, ct x pt" % (gp.K, rot_base),
+            "variant": "lazy accumulation (group sums of weight plaintexts, digit-by-digit rotation merge)",
+            "matches": st["matches"], "groups": st["rescales"], "ks_final": st["ks_final"],
+            "ms": ms, "products_per_s": 1e3 / ms, "warmup": 0, "max_abs_err": err, "keygen_s": round(keygen_s, 2)}
+
+
 def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
     """Poisson stream of `count` requests (d from `dims`, sparsity U[0.5,0.95],
     remaining levels U{10..30}, 4 key sets) on the serving ring (N=2^16, L=31,
-    dnum=4): the continuous-batching server against a plain loop that runs each
-    request alone in arrival order.  Latency = completion - arrival."""
+    dnum=4): the continuous-batching server against the plain path, which runs
+    each request alone in arrival order with Alg. 2 op by op (one match per
+    launch sequence).  Latency = completion - arrival; at an offered rate
+    above both capacities, throughput = capacity."""
     import torch
     from paper_2604_11659_gb300 import params as gparams
     from paper_2604_11659_gb300 import spfhe as sp
@@ -342,8 +402,9 @@ def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
     prods = [_encrypt_case(sp, ctx, keysets[r.key_set], r.case, r.level, rec.scale, 10 * i) for i, r in enumerate(reqs)]
     torch.cuda.synchronize()
     matches = 0
-    # plain: one request at a time, in arrival order, each alone
+    # plain: one request at a time, in arrival order, each alone, op by op
     lat_plain = []
+    sp.spfhe_ctx_set_match_batch(ctx, 1)
     t0 = time.perf_counter()
     for r, (Am, a, Bm, b, nc) in zip(reqs, prods):
         now = time.perf_counter() - t0
@@ -355,6 +416,7 @@ def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
         for h in outs:
             sp.spfhe_ct_free(h)
     plain_total = time.perf_counter() - t0
+    sp.spfhe_ctx_set_match_batch(ctx, 0)
     # served
     srv = sp.spfhe_server_create(ctx, 64 << 30)
     tickets = []
@@ -383,7 +445,7 @@ def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
     q = lambda xs, p: float(np.percentile(np.array(xs) * 1e3, p))
     return {"workload": "%d requests, Poisson %.1f/s, d in %s, sparsity U[0.5,0.95], levels U{10..30}, 4 key sets, "
                         "N=2^16, L=31, dnum=4 (scaled from 2000 requests of d in {64..512})" % (count, rate, list(dims)),
-            "matches": matches,
+            "matches": matches, "plain_path": "each request alone in arrival order, one match per launch sequence",
             "served": {"p50_ms": q(lat_served, 50), "p99_ms": q(lat_served, 99), "requests_per_s": count / served_total},
             "plain": {"p50_ms": q(lat_plain, 50), "p99_ms": q(lat_plain, 99), "requests_per_s": count / plain_total},
             "throughput_speedup": plain_total / served_total}
@@ -538,7 +600,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-products", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--dense-layer", type=int, default=1,
+                    help="1: run the N=2^17 dense-layer ct x pt product once (lazy accumulation)")
     ap.add_argument("--grouped-steps", type=int, default=2,
                     help="timed steps of the lazy-accumulation variant (0: skip)")
     ap.add_argument("--ntt-chunk", type=int, default=-1,
@@ -726,6 +790,8 @@ def main():
         line["batch"] = batch_vs_plain(stream, args.batch_products, (8, 16), ntt=g.ntt_chunk)
     if args.serve_requests > 0:
         line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
+    if args.dense_layer:
+        line["dense_layer_ct_pt"] = dense_layer_pt(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(case, args.rot_base)
     if rank == 0:

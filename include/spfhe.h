@@ -328,6 +328,21 @@ spfhe_status spfhe_sparse_matmul_ct_ct_grouped(spfhe_ctx *ctx, const spfhe_keys 
                                                const spfhe_pt *mask0, int merge_digits, spfhe_ct **C_chunks,
                                                size_t n_c, spfhe_stats *stats);
 
+/* Lazy-accumulation variant of spfhe_sparse_matmul_ct_pt (a library
+ * extension that reorders the ct x pt products; the paper has no
+ * counterpart).  The weight plaintexts B[k, j] e_{a_slot} of the matches that
+ * share the result chunk and the final rotation amount r are summed per A
+ * chunk, each sum multiplies its chunk, a group's products are added,
+ * rescaled once and rotated as in spfhe_sparse_matmul_ct_ct_grouped (digit by
+ * digit when merge_digits != 0).  Arguments, result level and scale as
+ * spfhe_sparse_matmul_ct_pt; stats: rescales counts groups.  Blocks until the
+ * result is ready. */
+spfhe_status spfhe_sparse_matmul_ct_pt_grouped(spfhe_ctx *ctx, const spfhe_keys *keys,
+                                               const spfhe_sparse_meta *A_csr, spfhe_ct *const *A_chunks, size_t n_a,
+                                               const spfhe_sparse_meta *B_csc, const double *B_values,
+                                               spfhe_pt *const *B_pts, int merge_digits, spfhe_ct **C_chunks,
+                                               size_t n_c, spfhe_stats *stats);
+
 /* NTT launch-chunk tuner (library extension; the paper has no tuner).  Times
  * the key-switching transforms of one match batch at level ell (forward NTT
  * of the ModUp extension of `items` polynomials, inverse NTT of their ell

@@ -592,6 +592,28 @@ spfhe_status spfhe_sparse_matmul_ct_ct_grouped(spfhe_ctx *ctx, const spfhe_keys 
     });
 }
 
+spfhe_status spfhe_sparse_matmul_ct_pt_grouped(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_sparse_meta *A_csr,
+                                               spfhe_ct *const *A_chunks, size_t n_a, const spfhe_sparse_meta *B_csc,
+                                               const double *B_values, spfhe_pt *const *B_pts, int merge_digits,
+                                               spfhe_ct **C_chunks, size_t n_c, spfhe_stats *stats)
+{
+    return guard([&] {
+        need(keys && A_csr && B_csc && A_chunks && C_chunks, "null argument");
+        need(n_a > 0, "no operand chunks");
+        Ctx &c = C(ctx);
+        std::vector<Ct *> a(n_a), out(n_c, nullptr);
+        for (size_t i = 0; i < n_a; ++i) a[i] = A_chunks[i] ? A_chunks[i]->c : nullptr;
+        std::vector<Pt *> bp;
+        if (B_pts) {
+            bp.resize(B_csc->nnz);
+            for (int i = 0; i < B_csc->nnz; ++i) bp[i] = B_pts[i] ? B_pts[i]->p : nullptr;
+        }
+        spmspm_ct_pt_grouped(c, *keys->k, *A_csr, a.data(), n_a, *B_csc, B_values, B_pts ? bp.data() : nullptr,
+                             merge_digits != 0, out.data(), n_c, stats);
+        for (size_t i = 0; i < n_c; ++i) C_chunks[i] = wrap(out[i]);
+    });
+}
+
 spfhe_status spfhe_sparse_matmul_ct_pt(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_sparse_meta *A_csr,
                                        spfhe_ct *const *A_chunks, size_t n_a, const spfhe_sparse_meta *B_csc,
                                        const double *B_values, spfhe_pt *const *B_pts, spfhe_ct **C_chunks,

@@ -117,7 +117,53 @@ __global__ void k_onehot0(int n, int ell, const double *vals, double c, const do
     if (x < 0) r = neg_mod(r, m.q);
     out[((size_t)it * ell + l) * n + j] = r;
 }
+// Coefficient-domain sums of one-hot encodings: segment s (blockIdx.z) of
+// items c = seg[s] .. seg[s+1]-1 gets sum_c sigma_{g_c}(m0(v_c))_j, where
+// m0(v) is k_onehot0's slot-0 encoding of v and sigma_g the automorphism
+// X -> X^g (coefficient i goes to i g mod 2n, negated past n), i.e. the
+// encoding of v_c at slot p_c for g_c = 5^-p_c.  ginv[c] = g_c^{-1} mod 2n.
+// The integer sum is exact; then its residue for every limb.
+__global__ void k_onehot_sum(int log_n, int ell, const int *seg, const double *vals, const int *ginv, double c,
+                             const double *cos_tab, u64 *out, const ModConst *__restrict__ mc)
+{
+    const int n = 1 << log_n;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int s = blockIdx.z;
+    long long acc = 0;
+    for (int it = seg[s]; it < seg[s + 1]; ++it) {
+        const unsigned i0 = (unsigned)(((unsigned long long)j * (unsigned)ginv[it]) & ((2ull << log_n) - 1));
+        const bool neg = i0 >= (unsigned)n;
+        const unsigned i = neg ? i0 - n : i0;
+        const double x = (vals[it] * c) * cos_tab[i];
+        long long a = (long long)floor(fabs(x) + 0.5);
+        if ((x < 0) != neg) a = -a;
+        acc += a;
+    }
+    const u64 mag = (u64)(acc < 0 ? -acc : acc);
+    for (int l = 0; l < ell; ++l) {
+        const ModConst m = mc[l];
+        u64 r = mul_shoup(redc(U128{mag, 0}, m.q, m.qneg_inv), m.r_mod, m.r_mod_p, m.q);
+        if (acc < 0) r = neg_mod(r, m.q);
+        out[((size_t)s * ell + l) * n + j] = r;
+    }
+}
 }  // namespace
+
+void encode_onehot_sums(Ctx &ctx, int segments, const int *d_seg, const double *d_values, const int *d_ginv, int ell,
+                        double scale, u64 *out)
+{
+    ensure_cos_table(ctx);
+    const double c = 2.0 * scale / ctx.n;
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_onehot_sum<<<dim3((ctx.n + 255) / 256, 1, segments), 256, 0, ctx.stream>>>(ctx.log_n, ell, d_seg, d_values,
+                                                                                    d_ginv, c, ctx.cos_tab, out,
+                                                                                    ctx.dt.mc);
+        prof_end(ctx, t0_, K_OTHER, 8.0 * ctx.n * ell * segments, 0.0, "one-hot sums");
+    }
+    ntt_forward(ctx, Batch{out, (long long)ell * ctx.n, segments, nullptr}, limb_range(0, ell, 0));
+}
 
 void encode_onehot0(Ctx &ctx, const double *d_values, int items, int ell, double scale, u64 *out)
 {

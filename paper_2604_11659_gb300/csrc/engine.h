@@ -99,9 +99,12 @@ size_t chunks_for(long long count, int S);
 // scales); returns the operands' level and their product's result scale
 int check_ct_ct(const Ctx &ctx, const spfhe_sparse_meta &A, const std::vector<Ct *> &Ach,
                 const spfhe_sparse_meta &B, const std::vector<Ct *> &Bch, size_t n_c, double *rscale);
-// lazy-accumulation variant of the ct x ct product (grouped.cpp)
+// lazy-accumulation variants of the products (grouped.cpp)
 void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
                           const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, bool merge_digits,
+                          Ct **C, size_t nC, spfhe_stats *out_stats);
+void spmspm_ct_pt_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
+                          const spfhe_sparse_meta &B, const double *Bvals, Pt *const *Bpts, bool merge_digits,
                           Ct **C, size_t nC, spfhe_stats *out_stats);
 size_t result_chunks(const Ctx &ctx, const spfhe_matmul_req &r);
 

@@ -1,26 +1,37 @@
-// Lazy-accumulation variant of the encrypted ct x ct product: a reordering
-// of Alg. 2 (not the paper's op order).
+// Lazy-accumulation variants of the encrypted products: reorderings of
+// Alg. 2 (not the paper's op order).
 //
-// Alignment rotations and tensor products are Alg. 2's.  Every tensor product
-// (three polynomials at the operands' level ell) is multiplied by its mask
-// e_{min_slot} (level ell, scale q_{ell-2}) and summed into the group of
-// matches sharing the result chunk and the final rotation amount r.  Each
-// group is then rescaled (three polynomials, level ell-1), relinearised at
-// level ell-1, rescaled again (level ell-2) and rotated:
-//   merge_digits: by the lowest base-b digit of r; the rotated groups are
-//     summed per (chunk, remaining amount) and each sum is rotated by its next
-//     digit, digit by digit, until nothing remains;
-//   otherwise: by the whole of r (its rotation plan);
-// and what remains is added into the result chunks.  Relinearisation and
-// rotation are linear, so the product decrypts like Alg. 2's; the number of
-// relinearisations drops from #matches to #groups and the final-rotation key
-// switches from the sum of the plan lengths to the digit tree's.
+// ct x ct: alignment rotations and tensor products are Alg. 2's.  Every
+// tensor product (three polynomials at the operands' level ell) is multiplied
+// by its mask e_{min_slot} (level ell, scale q_{ell-2}) and summed into the
+// group of matches sharing the result chunk and the final rotation amount r.
+// Each group is rescaled (three polynomials, level ell-1), relinearised at
+// level ell-1, rescaled again (level ell-2) and handed to the rotation tree.
 //
-// Memory: every distinct alignment rotation is kept for the whole call (the
-// groups meet them in any order); groups run in batches; with merge_digits
-// the accumulators of the second tree level are all live.  Both are checked
-// against the free device memory before any launch (ENOMEM otherwise).
+// ct x pt (reading R9's products): the weight plaintexts B[k, j] e_{a_slot}
+// of a group's matches are summed per A chunk, each sum multiplies its chunk,
+// the products are added, rescaled once (level L-1) and handed to the tree.
+// With the library's own weights, a sub-group's summed plaintext is encoded
+// in one pass (coefficient-domain sum of the permuted one-hot encodings, one
+// transform) instead of one encoding and transform per match.
+//
+// Rotation tree: merge_digits rotates each group by the lowest base-b digit
+// of r, sums the results per (chunk, remaining amount) and rotates each sum
+// by its next digit, digit by digit, until nothing remains; otherwise every
+// group is rotated by the whole of r.  What remains is added into the result
+// chunks.  Relinearisation and rotation are linear, so the products decrypt
+// like Alg. 2's, with fewer key switches; the ciphertext bits differ.
+//
+// Groups arrive at the tree in ascending (chunk, r) order, so a sum of the
+// tree is complete as soon as the stream has passed its range of amounts and
+// no sum at a lower level within that range is still pending; sums are
+// rotated in batches as they complete, which bounds the tree's memory for
+// any base.  The ct x ct
+// variant keeps every distinct alignment rotation of the call in device memory
+// (checked against the free memory before any launch: ENOMEM otherwise).
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstring>
 #include <map>
 
@@ -30,18 +41,7 @@ namespace spfhe {
 
 namespace {
 
-struct GMatch {
-    int src_a, src_b;   // >= 0: alignment store slot; < 0: -(chunk + 1)
-    int min_slot;
-};
-
-struct Group {
-    int rc, r;
-    std::vector<int> matches;
-};
-
-// digit of r at weight w in base b
-int digit_at(long long r, long long w, long long b) { return (int)((r / w) % b); }
+using Key = std::pair<int, long long>;   // (result chunk, amount)
 
 void need_memory(size_t bytes, const char *what)
 {
@@ -51,6 +51,243 @@ void need_memory(size_t bytes, const char *what)
     if (bytes + margin > free_b)
         throw Error(SPFHE_ENOMEM, std::string(what) + " needs " + std::to_string(bytes >> 20) + " MiB, " +
                                       std::to_string(free_b >> 20) + " MiB free");
+}
+
+// tgt[i] (+)= sum of srcs[i]; fresh targets start at zero
+void sum_into(Ctx &ctx, int polys, int ell, const std::vector<u64 *> &tgt,
+              const std::vector<std::vector<const u64 *>> &srcs, const std::vector<char> &fresh)
+{
+    Runtime &rt = *ctx.rt;
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<u64 *> t;
+        std::vector<const u64 *> s;
+        std::vector<int> seg{0};
+        for (size_t i = 0; i < tgt.size(); ++i) {
+            if ((fresh[i] != 0) != (pass == 0)) continue;
+            t.push_back(tgt[i]);
+            for (const u64 *p : srcs[i]) s.push_back(p);
+            seg.push_back((int)s.size());
+        }
+        if (t.empty()) continue;
+        accumulate_seg(ctx, polys, ell, (int)t.size(), rt.upload_vec(t), rt.upload_vec(s), rt.upload_vec(seg),
+                       (int)s.size(), pass == 1);
+    }
+}
+
+// Streaming rotation tree over ciphertexts at level lv (see the file comment).
+class DigitTree {
+  public:
+    DigitTree(Ctx &ctx, const Keys &keys, int lv, bool merge, const std::vector<Ct *> &res)
+        : ctx_(ctx), keys_(keys), lv_(lv), merge_(merge), res_(res), b_(ctx.rot_base), S_(ctx.S),
+          cs_(2LL * lv * ctx.n), bm_(match_batch_size(ctx))
+    {
+        digits_ = 0;
+        for (long long w = 1; w < S_; w *= b_) ++digits_;
+        levels_.resize(std::max(digits_, 1));
+    }
+    ~DigitTree()
+    {
+        for (u64 *p : all_) dev_free(ctx_, p);
+    }
+    // every key the tree will use for an item of amount r
+    static void check_keys(const Ctx &ctx, const Keys &keys, long long r, bool merge)
+    {
+        if (!merge) {
+            for (int s : rotation_plan(ctx, r)) rotation_key(keys, s);
+            return;
+        }
+        for (long long w = 1; w < ctx.S; w *= ctx.rot_base) {
+            const int d = (int)((r / w) % ctx.rot_base);
+            if (d) rotation_key(keys, (int)(d * w));
+        }
+    }
+    // items in ascending (chunk, r) order; `next` = the key of the first item
+    // not pushed yet ({INT_MAX, 0} when none follows)
+    void push(const std::vector<Key> &key, const std::vector<const u64 *> &ct, Key next)
+    {
+        const int k = (int)key.size();
+        if (!k) return;
+        Runtime &rt = *ctx_.rt;
+        u64 *out = rt.workspace(WS_TREE_ROT, (size_t)k * cs_);
+        std::vector<const u64 *> src(ct);
+        if (!merge_) {
+            std::vector<int> amt(k);
+            for (int i = 0; i < k; ++i) amt[i] = (int)key[i].second;
+            rotate_batch(ctx_, keys_, lv_, ct, amt, out, &ks);
+            for (int i = 0; i < k; ++i) src[i] = out + (long long)i * cs_;
+            add_to_results(key, src);
+            return;
+        }
+        rotate_digit(key, src, 1, out);
+        route(key, src, 1, 1);
+        flush(next, false);
+    }
+    void finish()
+    {
+        if (merge_) flush(Key{INT_MAX, 0}, true);
+    }
+    uint64_t ks = 0;
+
+  private:
+    Ctx &ctx_;
+    const Keys &keys_;
+    int lv_;
+    bool merge_;
+    const std::vector<Ct *> &res_;
+    long long b_, S_, cs_;
+    int bm_, digits_;
+    // levels_[t]: sums whose amounts have their t lowest digits removed
+    std::vector<std::map<Key, u64 *>> levels_;
+    std::vector<u64 *> pool_, all_;
+
+    u64 *get()
+    {
+        if (!pool_.empty()) {
+            u64 *p = pool_.back();
+            pool_.pop_back();
+            return p;
+        }
+        u64 *p = static_cast<u64 *>(dev_alloc(ctx_, (size_t)cs_ * sizeof(u64)));
+        all_.push_back(p);
+        return p;
+    }
+    long long weight(int t) const
+    {
+        long long w = 1;
+        for (int i = 0; i < t; ++i) w *= b_;
+        return w;
+    }
+    int digit(long long r, long long w) const { return (int)((r / w) % b_); }
+    // rotate src[i] by its key's digit at weight w (those with a nonzero
+    // digit); the rotated ciphertexts go to out and replace src[i]
+    void rotate_digit(const std::vector<Key> &key, std::vector<const u64 *> &src, long long w, u64 *out)
+    {
+        std::vector<int> rid;
+        for (size_t i = 0; i < key.size(); ++i)
+            if (digit(key[i].second, w)) rid.push_back((int)i);
+        if (rid.empty()) return;
+        // equal keys next to each other for the inner product
+        std::stable_sort(rid.begin(), rid.end(),
+                         [&](int x, int y) { return digit(key[x].second, w) < digit(key[y].second, w); });
+        std::vector<const u64 *> sin, skey;
+        std::vector<int> sg;
+        for (int i : rid) {
+            const int d = digit(key[i].second, w);
+            sin.push_back(src[i]);
+            sg.push_back(galois_element(ctx_, (int)(d * w)));
+            skey.push_back(rotation_key(keys_, (int)(d * w)));
+        }
+        rotate_step_batch(ctx_, lv_, sin, sg, skey, out);
+        ks += sin.size();
+        for (size_t j = 0; j < rid.size(); ++j) src[rid[j]] = out + (long long)j * cs_;
+    }
+    // add each (rotated) item into its sum at level t (amount minus its digit
+    // at weight w), or into its result chunk when nothing remains
+    void route(const std::vector<Key> &key, const std::vector<const u64 *> &src, int t, long long w)
+    {
+        std::map<Key, std::vector<const u64 *>> to_level;
+        std::map<int, std::vector<const u64 *>> to_res;
+        for (size_t i = 0; i < key.size(); ++i) {
+            const long long rem = key[i].second - digit(key[i].second, w) * w;
+            if (rem == 0) to_res[key[i].first].push_back(src[i]);
+            else to_level[{key[i].first, rem}].push_back(src[i]);
+        }
+        std::vector<u64 *> tgt;
+        std::vector<std::vector<const u64 *>> srcs;
+        std::vector<char> fresh;
+        for (auto &kv : to_level) {
+            auto it = levels_[t].find(kv.first);
+            const bool f = it == levels_[t].end();
+            u64 *p = f ? (levels_[t][kv.first] = get()) : it->second;
+            tgt.push_back(p);
+            srcs.push_back(kv.second);
+            fresh.push_back(f ? 1 : 0);
+        }
+        for (auto &kv : to_res) {
+            tgt.push_back(res_[kv.first]->d);
+            srcs.push_back(kv.second);
+            fresh.push_back(0);
+        }
+        sum_into(ctx_, 2, lv_, tgt, srcs, fresh);
+    }
+    void add_to_results(const std::vector<Key> &key, const std::vector<const u64 *> &src)
+    {
+        std::map<int, std::vector<const u64 *>> by;
+        for (size_t i = 0; i < key.size(); ++i) by[key[i].first].push_back(src[i]);
+        std::vector<u64 *> tgt;
+        std::vector<std::vector<const u64 *>> srcs;
+        for (auto &kv : by) {
+            tgt.push_back(res_[kv.first]->d);
+            srcs.push_back(kv.second);
+        }
+        sum_into(ctx_, 2, lv_, tgt, srcs, std::vector<char>(tgt.size(), 0));
+    }
+    // rotate every complete sum by its next digit and pass it on (at least
+    // bm_ sums of a level at a time unless forced)
+    void flush(Key next, bool force)
+    {
+        for (int t = 1; t < digits_; ++t) {
+            const long long w = weight(t);
+            std::vector<Key> done;
+            for (auto &kv : levels_[t]) {
+                const Key &k = kv.first;
+                // every group of amounts [k.second, k.second + w) has been pushed ...
+                const Key end{k.first, k.second + w};
+                if (!force && next < end) break;
+                // ... and no sum at any lower level is still on its way to it
+                bool fed = false;
+                for (int u = 1; u < t && !fed; ++u) {
+                    auto lo = levels_[u].lower_bound(k);
+                    fed = lo != levels_[u].end() && lo->first < end;
+                }
+                if (fed) break;
+                done.push_back(k);
+            }
+            if (done.empty() || (!force && (int)done.size() < bm_)) continue;
+            for (size_t d0 = 0; d0 < done.size(); d0 += bm_) {
+                const size_t d1 = std::min(done.size(), d0 + bm_);
+                std::vector<Key> key(done.begin() + d0, done.begin() + d1);
+                std::vector<const u64 *> src;
+                std::vector<u64 *> owned;
+                for (const Key &k : key) {
+                    owned.push_back(levels_[t][k]);
+                    src.push_back(levels_[t][k]);
+                    levels_[t].erase(k);
+                }
+                u64 *out = ctx_.rt->workspace(WS_TREE_ROT, key.size() * (size_t)cs_);
+                rotate_digit(key, src, w, out);
+                route(key, src, t + 1 < digits_ ? t + 1 : t, w);
+                for (u64 *p : owned) pool_.push_back(p);
+            }
+        }
+    }
+};
+
+struct PlanMatch {
+    int src_a, src_b;   // >= 0 alignment store slot, < 0: -(chunk + 1)
+    int slot;           // min_slot
+};
+
+void fill_stats(spfhe_stats *st, uint64_t matches, uint64_t relin, uint64_t align, uint64_t fin, uint64_t resc,
+                uint64_t launches)
+{
+    if (!st) return;
+    st->matches = matches;
+    st->ks_relin = relin;
+    st->ks_align = align;
+    st->ks_final = fin;
+    st->rescales = resc;
+    st->launches = launches;
+}
+
+void free_results(Ctx &ctx, std::vector<Ct *> &res)
+{
+    for (Ct *&c : res)
+        if (c) {
+            dev_free(ctx, c->d);
+            delete c;
+            c = nullptr;
+        }
 }
 
 }  // namespace
@@ -63,7 +300,6 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
     Runtime &rt = *ctx.rt;
     const int S = ctx.S;
     const size_t n = ctx.n;
-    const long long b = ctx.rot_base;
     for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
     std::vector<Ct *> av(Ach, Ach + nA), bv(Bch, Bch + nB);
     double rscale = 0;
@@ -72,18 +308,17 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
     const long long csL = 2LL * ell * n, cs1 = 2LL * (ell - 1) * n, cs2 = 2LL * (ell - 2) * n;
     const long long t3L = 3LL * ell * n, t31 = 3LL * (ell - 1) * n;
 
-    // ---- plan: alignments, matches, groups ----
+    // ---- plan: alignments, matches, groups in (chunk, amount) order ----
     const std::vector<MatchRec> ms = plan_alg1(A, B);
     if (!ms.empty() && !keys.relin) throw Error(SPFHE_EKEY, "no relinearisation key");
     std::map<std::tuple<int, int, int>, int> align_id;
     std::vector<std::tuple<int, int, int>> aligns;
-    std::vector<GMatch> gm(ms.size());
-    std::map<std::pair<int, int>, int> group_id;
-    std::vector<Group> groups;
+    std::vector<PlanMatch> pm(ms.size());
+    std::map<Key, std::vector<int>> groups;
     for (size_t x = 0; x < ms.size(); ++x) {
         const MatchRec &mt = ms[x];
         const int ca = mt.a_pos / S, sa = mt.a_pos % S, cb = mt.b_pos / S, sb = mt.b_pos % S;
-        GMatch g{-(ca + 1), -(cb + 1), std::min(sa, sb)};
+        PlanMatch g{-(ca + 1), -(cb + 1), std::min(sa, sb)};
         auto slot = [&](int op, int chunk, int amt) {
             const auto key = std::make_tuple(op, chunk, amt);
             auto it = align_id.find(key);
@@ -95,47 +330,20 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
         };
         if (sa < sb) g.src_b = slot(1, cb, sb - sa);
         else if (sb < sa) g.src_a = slot(0, ca, sa - sb);
-        gm[x] = g;
+        pm[x] = g;
         const long long t = (long long)mt.i * B.cols + mt.j;
-        const int rc = (int)(t / S), r = (int)(((g.min_slot - t % S) % S + S) % S);
-        auto it = group_id.find({rc, r});
-        int gid;
-        if (it == group_id.end()) {
-            gid = (int)groups.size();
-            group_id[{rc, r}] = gid;
-            groups.push_back(Group{rc, r, {}});
-        } else {
-            gid = it->second;
-        }
-        groups[gid].matches.push_back((int)x);
+        groups[{(int)(t / S), ((g.slot - t % S) % S + S) % S}].push_back((int)x);
     }
-    // groups in (chunk, amount) order
-    std::vector<int> gorder;
-    for (auto &kv : group_id) gorder.push_back(kv.second);
     // every key the call will use, before anything is launched
     for (auto &a : aligns)
         for (int s : rotation_plan(ctx, std::get<2>(a))) rotation_key(keys, s);
-    std::map<std::pair<int, long long>, int> stage1;   // (chunk, remaining) -> accumulator index
-    for (const Group &g : groups) {
-        if (merge) {
-            const int d0 = (int)(g.r % b);
-            if (d0) rotation_key(keys, d0);
-            stage1.emplace(std::make_pair(g.rc, (long long)g.r - d0), 0);
-            for (long long w = b; w < S; w *= b) {
-                const int d = digit_at(g.r, w, b);
-                if (d) rotation_key(keys, (int)(d * w));
-            }
-        } else {
-            for (int s : rotation_plan(ctx, g.r)) rotation_key(keys, s);
-        }
-    }
-    need_memory(aligns.size() * (size_t)csL * sizeof(u64) + (merge ? stage1.size() * (size_t)cs2 * sizeof(u64) : 0),
-                "the alignment store and digit-tree accumulators");
+    for (auto &kv : groups) DigitTree::check_keys(ctx, keys, kv.first.second, merge);
+    need_memory(aligns.size() * (size_t)csL * sizeof(u64), "the alignment store");
 
-    Scratch sc(ctx);
-    uint64_t st_align = 0, st_final = 0, st_relin = 0, st_rescales = 0;
+    uint64_t st_align = 0, st_relin = 0, st_rescales = 0, st_final = 0;
     std::vector<Ct *> res(nC, nullptr);
     try {
+        Scratch sc(ctx);
         for (size_t c = 0; c < nC; ++c) {
             res[c] = ct_new(ctx, ell - 2, rscale);
             SPFHE_CHECK_CUDA(cudaMemsetAsync(res[c]->d, 0, (size_t)cs2 * sizeof(u64), ctx.stream));
@@ -173,86 +381,68 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
                 return store + (long long)src * csL;
             };
 
-            // ---- tree accumulators of the second level ----
-            std::vector<u64 *> acc1;
-            if (merge) {
-                int k = 0;
-                for (auto &kv : stage1) {
-                    kv.second = k++;
-                    u64 *p = sc.words((size_t)cs2);
-                    SPFHE_CHECK_CUDA(cudaMemsetAsync(p, 0, (size_t)cs2 * sizeof(u64), ctx.stream));
-                    acc1.push_back(p);
-                }
-            }
-
-            // ---- groups in batches of up to Bm ----
+            DigitTree tree(ctx, keys, ell - 2, merge, res);
+            std::vector<const std::pair<const Key, std::vector<int>> *> gl;
+            for (auto &kv : groups) gl.push_back(&kv);
             const size_t max_matches = (size_t)2 * Bm;
-            for (size_t gi = 0; gi < gorder.size(); gi += Bm) {
-                std::vector<int> bg(gorder.begin() + gi, gorder.begin() + std::min(gorder.size(), gi + Bm));
-                const int k = (int)bg.size();
+            for (size_t gi = 0; gi < gl.size(); gi += Bm) {
+                const size_t ge = std::min(gl.size(), gi + Bm);
+                const int k = (int)(ge - gi);
                 u64 *G = rt.workspace(WS_GRP_SUM, (size_t)k * t3L);
                 u64 *R1 = rt.workspace(WS_LEVEL1, (size_t)k * t31);
                 u64 *R2 = rt.workspace(WS_LEVEL2, (size_t)k * cs1);
                 u64 *T = rt.workspace(WS_RS_TMP, (size_t)k * t3L);
                 u64 *X = rt.workspace(WS_RELIN_OUT, (size_t)k * cs2);
-                u64 *Y = rt.workspace(WS_MISC, (size_t)k * cs2);
                 // tensor products and masks of the batch's matches, at most
                 // max_matches at a time, summed into their groups
                 std::vector<std::pair<int, int>> flat;   // (group in batch, match)
                 for (int g = 0; g < k; ++g)
-                    for (int x : groups[bg[g]].matches) flat.push_back({g, x});
+                    for (int x : gl[gi + g]->second) flat.push_back({g, x});
                 std::vector<char> started(k, 0);
                 for (size_t f0 = 0; f0 < flat.size(); f0 += max_matches) {
                     const size_t f1 = std::min(flat.size(), f0 + max_matches);
                     const int m = (int)(f1 - f0);
                     u64 *D = rt.workspace(WS_TENSOR, (size_t)m * t3L);
-                    std::vector<const u64 *> pa, pb, mk, dsrc;
+                    std::vector<const u64 *> pa, pb, mk;
                     std::vector<int> gal;
                     for (size_t f = f0; f < f1; ++f) {
-                        const int x = flat[f].second;
-                        pa.push_back(operand(gm[x].src_a, true));
-                        pb.push_back(operand(gm[x].src_b, false));
+                        const PlanMatch &x = pm[flat[f].second];
+                        pa.push_back(operand(x.src_a, true));
+                        pb.push_back(operand(x.src_b, false));
                         mk.push_back(mask);
                         // the mask for slot p is sigma_h of the slot-0 mask, h = 5^-p
-                        gal.push_back(galois_element(ctx, -gm[x].min_slot));
-                        dsrc.push_back(D + (long long)(f - f0) * t3L);
+                        gal.push_back(galois_element(ctx, -x.slot));
                     }
                     tensor(ctx, m, ell, rt.upload_vec(pa), rt.upload_vec(pb), D);
                     mul_plain_perm(ctx, m, ell, D, t3L, rt.upload_vec(mk), rt.upload_vec(gal), 3);
-                    // segments: runs of equal group (flat is in group order); a
-                    // group continued from the previous piece adds to its sum
-                    std::vector<u64 *> fresh_t, cont_t;
-                    std::vector<const u64 *> fresh_s, cont_s;
-                    std::vector<int> fresh_seg{0}, cont_seg{0};
+                    std::vector<u64 *> tgt;
+                    std::vector<std::vector<const u64 *>> srcs;
+                    std::vector<char> fresh;
                     for (size_t f = f0; f < f1;) {
                         const int g = flat[f].first;
                         size_t e = f;
                         while (e < f1 && flat[e].first == g) ++e;
-                        auto &tt = started[g] ? cont_t : fresh_t;
-                        auto &ss = started[g] ? cont_s : fresh_s;
-                        auto &sg = started[g] ? cont_seg : fresh_seg;
-                        tt.push_back(G + (long long)g * t3L);
-                        for (size_t q = f; q < e; ++q) ss.push_back(dsrc[q - f0]);
-                        sg.push_back((int)ss.size());
+                        tgt.push_back(G + (long long)g * t3L);
+                        srcs.emplace_back();
+                        for (size_t q = f; q < e; ++q) srcs.back().push_back(D + (long long)(q - f0) * t3L);
+                        fresh.push_back(started[g] ? 0 : 1);
                         started[g] = 1;
                         f = e;
                     }
-                    if (!fresh_t.empty())
-                        accumulate_seg(ctx, 3, ell, (int)fresh_t.size(), rt.upload_vec(fresh_t),
-                                       rt.upload_vec(fresh_s), rt.upload_vec(fresh_seg), (int)fresh_s.size(), false);
-                    if (!cont_t.empty())
-                        accumulate_seg(ctx, 3, ell, (int)cont_t.size(), rt.upload_vec(cont_t), rt.upload_vec(cont_s),
-                                       rt.upload_vec(cont_seg), (int)cont_s.size(), true);
+                    sum_into(ctx, 3, ell, tgt, srcs, fresh);
                 }
                 // rescale of the three polynomials, relinearisation at level
                 // ell-1 (key switch of the s^2 part, added to the first two),
                 // rescale of the ciphertext
-                std::vector<const u64 *> g0(k), d2(k), base(k), x1(k);
+                std::vector<const u64 *> g0(k), d2(k), base(k), x1(k), x2(k);
+                std::vector<Key> key(k);
                 for (int g = 0; g < k; ++g) {
                     g0[g] = G + (long long)g * t3L;
                     base[g] = R1 + (long long)g * t31;
                     d2[g] = base[g] + 2LL * (ell - 1) * n;
                     x1[g] = R2 + (long long)g * cs1;
+                    x2[g] = X + (long long)g * cs2;
+                    key[g] = gl[gi + g]->first;
                 }
                 rescale(ctx, k, ell, rt.upload_vec(g0), T, R1, t31, 3);
                 std::vector<KeyGroup> kg;
@@ -261,151 +451,176 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
                 st_relin += k;
                 rescale(ctx, k, ell - 1, rt.upload_vec(x1), T, X, cs2, 2);
                 st_rescales += 2ull * k;
-                // rotation by the lowest digit (merge) or the whole amount
-                std::vector<const u64 *> src(k);
-                for (int g = 0; g < k; ++g) src[g] = X + (long long)g * cs2;
-                if (merge) {
-                    std::vector<const u64 *> rin, rkey;
-                    std::vector<int> rg, rid;
-                    for (int g = 0; g < k; ++g) {
-                        const int d0 = (int)(groups[bg[g]].r % b);
-                        if (!d0) continue;
-                        rin.push_back(src[g]);
-                        rg.push_back(galois_element(ctx, d0));
-                        rkey.push_back(rotation_key(keys, d0));
-                        rid.push_back(g);
-                    }
-                    // equal keys next to each other for the inner product
-                    std::vector<int> ord(rid.size());
-                    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-                    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return rkey[x] < rkey[y]; });
-                    std::vector<const u64 *> sin, skey;
-                    std::vector<int> sg;
-                    for (int i : ord) {
-                        sin.push_back(rin[i]);
-                        sg.push_back(rg[i]);
-                        skey.push_back(rkey[i]);
-                    }
-                    rotate_step_batch(ctx, ell - 2, sin, sg, skey, Y);
-                    st_final += sin.size();
-                    for (size_t i = 0; i < ord.size(); ++i) src[rid[ord[i]]] = Y + (long long)i * cs2;
-                    // sums per (chunk, remaining amount)
-                    std::map<int, std::vector<int>> by_acc;
-                    for (int g = 0; g < k; ++g) {
-                        const Group &gr = groups[bg[g]];
-                        by_acc[stage1.at({gr.rc, (long long)gr.r - gr.r % b})].push_back(g);
-                    }
-                    std::vector<u64 *> tg;
-                    std::vector<const u64 *> ss;
-                    std::vector<int> sg2{0};
-                    for (auto &kv : by_acc) {
-                        tg.push_back(acc1[kv.first]);
-                        for (int g : kv.second) ss.push_back(src[g]);
-                        sg2.push_back((int)ss.size());
-                    }
-                    accumulate_seg(ctx, 2, ell - 2, (int)tg.size(), rt.upload_vec(tg), rt.upload_vec(ss),
-                                   rt.upload_vec(sg2), (int)ss.size(), true);
-                } else {
-                    std::vector<int> amt(k);
-                    for (int g = 0; g < k; ++g) amt[g] = groups[bg[g]].r;
-                    rotate_batch(ctx, keys, ell - 2, src, amt, Y, &st_final);
-                    std::map<int, std::vector<int>> by_chunk;
-                    for (int g = 0; g < k; ++g) by_chunk[groups[bg[g]].rc].push_back(g);
-                    std::vector<u64 *> tg;
-                    std::vector<const u64 *> ss;
-                    std::vector<int> sg2{0};
-                    for (auto &kv : by_chunk) {
-                        tg.push_back(res[kv.first]->d);
-                        for (int g : kv.second) ss.push_back(Y + (long long)g * cs2);
-                        sg2.push_back((int)ss.size());
-                    }
-                    accumulate_seg(ctx, 2, ell - 2, (int)tg.size(), rt.upload_vec(tg), rt.upload_vec(ss),
-                                   rt.upload_vec(sg2), (int)ss.size(), true);
-                }
+                tree.push(key, x2, ge < gl.size() ? gl[ge]->first : Key{INT_MAX, 0});
             }
-
-            // ---- digit tree: rotate each sum by its next digit and merge ----
-            if (merge) {
-                std::map<std::pair<int, long long>, u64 *> live;
-                for (auto &kv : stage1) live[kv.first] = acc1[kv.second];
-                for (long long w = b; w < S; w *= b) {
-                    bool rest = false;
-                    for (auto &kv : live) rest = rest || kv.first.second != 0;
-                    if (!rest) break;
-                    std::map<std::pair<int, long long>, std::vector<const u64 *>> next_src;
-                    std::vector<std::pair<int, long long>> keys_v;
-                    for (auto &kv : live) keys_v.push_back(kv.first);
-                    for (size_t k0 = 0; k0 < keys_v.size(); k0 += Bm) {
-                        const size_t k1 = std::min(keys_v.size(), k0 + Bm);
-                        std::vector<const u64 *> sin, skey;
-                        std::vector<int> sg;
-                        std::vector<size_t> rid;
-                        for (size_t x = k0; x < k1; ++x) {
-                            const int d = digit_at(keys_v[x].second, w, b);
-                            if (!d) continue;
-                            sin.push_back(live[keys_v[x]]);
-                            sg.push_back(galois_element(ctx, (int)(d * w)));
-                            skey.push_back(rotation_key(keys, (int)(d * w)));
-                            rid.push_back(x);
-                        }
-                        if (!sin.empty()) {
-                            u64 *out = sc.words(sin.size() * (size_t)cs2);
-                            rotate_step_batch(ctx, ell - 2, sin, sg, skey, out);
-                            st_final += sin.size();
-                            for (size_t i = 0; i < rid.size(); ++i) live[keys_v[rid[i]]] = out + (long long)i * cs2;
-                        }
-                    }
-                    for (auto &kv : live) {
-                        const int d = digit_at(kv.first.second, w, b);
-                        next_src[{kv.first.first, kv.first.second - d * w}].push_back(kv.second);
-                    }
-                    std::map<std::pair<int, long long>, u64 *> nl;
-                    std::vector<u64 *> tg;
-                    std::vector<const u64 *> ss;
-                    std::vector<int> sg2{0};
-                    for (auto &kv : next_src) {
-                        u64 *p = sc.words((size_t)cs2);
-                        nl[kv.first] = p;
-                        tg.push_back(p);
-                        for (const u64 *q : kv.second) ss.push_back(q);
-                        sg2.push_back((int)ss.size());
-                    }
-                    accumulate_seg(ctx, 2, ell - 2, (int)tg.size(), rt.upload_vec(tg), rt.upload_vec(ss),
-                                   rt.upload_vec(sg2), (int)ss.size(), false);
-                    live.swap(nl);
-                }
-                std::map<int, std::vector<const u64 *>> by_chunk;
-                for (auto &kv : live) by_chunk[kv.first.first].push_back(kv.second);
-                std::vector<u64 *> tg;
-                std::vector<const u64 *> ss;
-                std::vector<int> sg2{0};
-                for (auto &kv : by_chunk) {
-                    tg.push_back(res[kv.first]->d);
-                    for (const u64 *q : kv.second) ss.push_back(q);
-                    sg2.push_back((int)ss.size());
-                }
-                accumulate_seg(ctx, 2, ell - 2, (int)tg.size(), rt.upload_vec(tg), rt.upload_vec(ss),
-                               rt.upload_vec(sg2), (int)ss.size(), true);
-            }
+            tree.finish();
+            st_final = tree.ks;
         }
         SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
     } catch (...) {
-        for (Ct *c : res)
-            if (c) {
-                dev_free(ctx, c->d);
-                delete c;
-            }
+        free_results(ctx, res);
         throw;
     }
     for (size_t c = 0; c < nC; ++c) C[c] = res[c];
-    if (out_stats) {
-        out_stats->matches = ms.size();
-        out_stats->ks_relin = st_relin;
-        out_stats->ks_align = st_align;
-        out_stats->ks_final = st_final;
-        out_stats->rescales = st_rescales;
-        out_stats->launches = ctx.launches - launches0;
+    fill_stats(out_stats, ms.size(), st_relin, st_align, st_final, st_rescales, ctx.launches - launches0);
+}
+
+void spmspm_ct_pt_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
+                          const spfhe_sparse_meta &B, const double *Bvals, Pt *const *Bpts, bool merge, Ct **C,
+                          size_t nC, spfhe_stats *out_stats)
+{
+    const uint64_t launches0 = ctx.launches;
+    Runtime &rt = *ctx.rt;
+    validate_pair(A, B);
+    const int S = ctx.S, L = ctx.L;
+    const size_t n = ctx.n;
+    if (L < 2) throw Error(SPFHE_ELEVEL, "ct x pt needs L >= 2");
+    if (nA != chunks_for(A.nnz, S)) throw Error(SPFHE_EINVAL, "operand chunk count != ceil(nnz / S)");
+    if (nC != chunks_for((long long)A.rows * B.cols, S))
+        throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
+    if (!Bvals && !Bpts && B.nnz > 0) throw Error(SPFHE_EINVAL, "B values missing");
+    for (size_t c = 0; c < nA; ++c)
+        if (!Ach[c] || !Ach[c]->d || Ach[c]->level != L) throw Error(SPFHE_ELEVEL, "A chunks must be at level L");
+    const double sa0 = Ach[0]->scale;
+    for (size_t c = 0; c < nA; ++c)
+        if (std::fabs(Ach[c]->scale - sa0) > 1e-9 * sa0) throw Error(SPFHE_ESCALE, "A chunk scales differ");
+    for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
+    const double wscale = (double)ctx.mods[L - 1];
+    const double rscale = sa0 * wscale / (double)ctx.mods[L - 1];
+    const long long csL = 2LL * L * n, cs1 = 2LL * (L - 1) * n, plimb = (long long)L * n;
+
+    const std::vector<MatchRec> ms = plan_alg1(A, B);
+    // groups -> sub-groups per A chunk -> matches, all in key order
+    std::map<Key, std::map<int, std::vector<int>>> groups;
+    for (size_t x = 0; x < ms.size(); ++x) {
+        const MatchRec &mt = ms[x];
+        const int ca = mt.a_pos / S, sa = mt.a_pos % S;
+        const long long t = (long long)mt.i * B.cols + mt.j;
+        groups[{(int)(t / S), ((sa - t % S) % S + S) % S}][ca].push_back((int)x);
     }
+    for (auto &kv : groups) DigitTree::check_keys(ctx, keys, kv.first.second, merge);
+    if (Bpts)
+        for (auto &mt : ms)
+            if (!Bpts[mt.b_pos] || Bpts[mt.b_pos]->level != L)
+                throw Error(SPFHE_ELEVEL, "B plaintexts must be at level L");
+
+    uint64_t st_rescales = 0, st_final = 0;
+    std::vector<Ct *> res(nC, nullptr);
+    std::vector<int> mi(L);
+    for (int i = 0; i < L; ++i) mi[i] = i;
+    try {
+        for (size_t c = 0; c < nC; ++c) {
+            res[c] = ct_new(ctx, L - 1, rscale);
+            SPFHE_CHECK_CUDA(cudaMemsetAsync(res[c]->d, 0, (size_t)cs1 * sizeof(u64), ctx.stream));
+        }
+        if (!ms.empty()) {
+            const int Bm = match_batch_size(ctx);
+            const size_t max_matches = (size_t)2 * Bm;
+            DigitTree tree(ctx, keys, L - 1, merge, res);
+            std::vector<const std::pair<const Key, std::map<int, std::vector<int>>> *> gl;
+            for (auto &kv : groups) gl.push_back(&kv);
+            for (size_t gi = 0; gi < gl.size(); gi += Bm) {
+                const size_t ge = std::min(gl.size(), gi + Bm);
+                const int k = (int)(ge - gi);
+                // sub-groups of the batch
+                std::vector<std::pair<int, int>> subs;   // (group in batch, A chunk)
+                std::vector<std::pair<int, int>> flat;   // (sub-group, match)
+                for (int g = 0; g < k; ++g)
+                    for (auto &sg : gl[gi + g]->second) {
+                        for (int x : sg.second) flat.push_back({(int)subs.size(), x});
+                        subs.push_back({g, sg.first});
+                    }
+                const int nsub = (int)subs.size();
+                u64 *PS = rt.workspace(WS_PTS, (size_t)nsub * plimb);        // summed weight plaintexts
+                u64 *X = rt.workspace(WS_GRP_SUM, (size_t)nsub * csL);       // chunk x plaintext products
+                u64 *G = rt.workspace(WS_RELIN_OUT, (size_t)k * csL);        // group sums
+                u64 *Y = rt.workspace(WS_LEVEL1, (size_t)k * cs1);           // rescaled
+                u64 *T = rt.workspace(WS_RS_TMP, (size_t)k * 2 * L * n);
+                std::vector<char> started(nsub, 0);
+                if (!Bpts) {
+                    // the library's own weights: each sub-group's plaintext is
+                    // encoded at once as its sum of permuted one-hot encodings
+                    std::vector<int> seg{0}, ginv;
+                    std::vector<double> vals;
+                    for (size_t f = 0; f < flat.size(); ++f) {
+                        const MatchRec &mt = ms[flat[f].second];
+                        vals.push_back(Bvals[mt.b_pos]);
+                        ginv.push_back(galois_element(ctx, mt.a_pos % S));
+                        if (f + 1 == flat.size() || flat[f + 1].first != flat[f].first) seg.push_back((int)vals.size());
+                    }
+                    encode_onehot_sums(ctx, nsub, rt.upload_vec(seg), rt.upload_vec(vals), rt.upload_vec(ginv), L,
+                                       wscale, PS);
+                    to_montgomery(ctx, PS, L, mi.data(), nsub);
+                }
+                for (size_t f0 = 0; Bpts && f0 < flat.size(); f0 += max_matches) {
+                    const size_t f1 = std::min(flat.size(), f0 + max_matches);
+                    const int m = (int)(f1 - f0);
+                    // weight plaintexts at slot 0 (Montgomery form), permuted to the match's slot
+                    u64 *W0 = rt.workspace(WS_MASK, (size_t)m * plimb);
+                    u64 *W = rt.workspace(WS_TENSOR, (size_t)m * plimb);
+                    for (size_t f = f0; f < f1; ++f)
+                        copy_words(ctx, W0 + (long long)(f - f0) * plimb, Bpts[ms[flat[f].second].b_pos]->d,
+                                   (size_t)plimb);
+                    to_montgomery(ctx, W0, L, mi.data(), m);
+                    std::vector<const u64 *> win(m);
+                    std::vector<int> gal(m);
+                    for (size_t f = f0; f < f1; ++f) {
+                        win[f - f0] = W0 + (long long)(f - f0) * plimb;
+                        // B[k, j] e_p is sigma_h of B[k, j] e_0, h = 5^-p
+                        gal[f - f0] = galois_element(ctx, -(ms[flat[f].second].a_pos % S));
+                    }
+                    automorph(ctx, m, 1, L, rt.upload_vec(win), 0, W, plimb, rt.upload_vec(gal));
+                    std::vector<u64 *> tgt;
+                    std::vector<std::vector<const u64 *>> srcs;
+                    std::vector<char> fresh;
+                    for (size_t f = f0; f < f1;) {
+                        const int sgi = flat[f].first;
+                        size_t e = f;
+                        while (e < f1 && flat[e].first == sgi) ++e;
+                        tgt.push_back(PS + (long long)sgi * plimb);
+                        srcs.emplace_back();
+                        for (size_t q = f; q < e; ++q) srcs.back().push_back(W + (long long)(q - f0) * plimb);
+                        fresh.push_back(started[sgi] ? 0 : 1);
+                        started[sgi] = 1;
+                        f = e;
+                    }
+                    sum_into(ctx, 1, L, tgt, srcs, fresh);
+                }
+                // chunk x summed plaintext, then the sum over a group's chunks
+                std::vector<const u64 *> ach(nsub), pts(nsub);
+                std::vector<int> ident(nsub, 1);
+                for (int i = 0; i < nsub; ++i) {
+                    ach[i] = Ach[subs[i].second]->d;
+                    pts[i] = PS + (long long)i * plimb;
+                }
+                gather_items(ctx, nsub, (size_t)csL, rt.upload_vec(ach), X, csL);
+                mul_plain_perm(ctx, nsub, L, X, csL, rt.upload_vec(pts), rt.upload_vec(ident), 2);
+                std::vector<u64 *> gt(k);
+                std::vector<std::vector<const u64 *>> gs(k);
+                for (int g = 0; g < k; ++g) gt[g] = G + (long long)g * csL;
+                for (int i = 0; i < nsub; ++i) gs[subs[i].first].push_back(X + (long long)i * csL);
+                sum_into(ctx, 2, L, gt, gs, std::vector<char>(k, 1));
+                std::vector<const u64 *> gp(k), yp(k);
+                std::vector<Key> key(k);
+                for (int g = 0; g < k; ++g) {
+                    gp[g] = G + (long long)g * csL;
+                    yp[g] = Y + (long long)g * cs1;
+                    key[g] = gl[gi + g]->first;
+                }
+                rescale(ctx, k, L, rt.upload_vec(gp), T, Y, cs1, 2);
+                st_rescales += k;
+                tree.push(key, yp, ge < gl.size() ? gl[ge]->first : Key{INT_MAX, 0});
+            }
+            tree.finish();
+            st_final = tree.ks;
+        }
+        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+    } catch (...) {
+        free_results(ctx, res);
+        throw;
+    }
+    for (size_t c = 0; c < nC; ++c) C[c] = res[c];
+    fill_stats(out_stats, ms.size(), 0, 0, st_final, st_rescales, ctx.launches - launches0);
 }
 
 }  // namespace spfhe

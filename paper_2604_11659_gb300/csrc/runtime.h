@@ -48,6 +48,7 @@ enum WsSlot {
     WS_PTS,
     WS_MISC,
     WS_GRP_SUM,
+    WS_TREE_ROT,
 };
 
 // ---- batched evaluator (ckks.cpp) ----
@@ -103,5 +104,10 @@ void decode_host(const Ctx &ctx, const std::vector<u64> &limb0, double scale, do
 void ensure_cos_table(Ctx &ctx);
 // device: out [items][ell][n] = residues of round_half_away(v_i * (2 scale/n) cos(pi j/n))
 void encode_onehot0(Ctx &ctx, const double *d_values, int items, int ell, double scale, u64 *out);
+// device: out [segments][ell][n] (evaluation rep.) = per segment, the sum of
+// the one-hot encodings of values[c] at slots p_c, each taken as the
+// automorphism 5^-p_c of the slot-0 encoding (d_ginv[c] = 5^p_c mod 2n)
+void encode_onehot_sums(Ctx &ctx, int segments, const int *d_seg, const double *d_values, const int *d_ginv, int ell,
+                        double scale, u64 *out);
 
 }  // namespace spfhe

@@ -109,6 +109,9 @@ _SIGS = [
                                                  ctypes.c_size_t, ctypes.POINTER(SparseMeta), c_dblp,
                                                  ctypes.POINTER(handle), ctypes.POINTER(handle), ctypes.c_size_t,
                                                  ctypes.POINTER(Stats)]),
+    ("spfhe_sparse_matmul_ct_pt_grouped", ctypes.c_int,
+     [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
+      c_dblp, ctypes.POINTER(handle), ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
     ("spfhe_sparse_matmul_ct_ct_grouped", ctypes.c_int,
      [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
       ctypes.POINTER(handle), ctypes.c_size_t, handle, ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t,
@@ -522,4 +525,16 @@ def spfhe_sparse_matmul_ct_pt(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta,
     bp = None if B_pts is None else _handles(B_pts)
     _check(lib().spfhe_sparse_matmul_ct_pt(ctx, keys, ctypes.byref(A), _handles(A_chunks), len(A_chunks),
                                            ctypes.byref(B), _dbl(bv), bp, outs, n_c, ctypes.byref(st)))
+    return [handle(outs[i]) for i in range(n_c)], st.as_dict()
+
+
+def spfhe_sparse_matmul_ct_pt_grouped(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta, B_values, B_pts, n_c: int,
+                                      merge_digits: bool = True):
+    outs = (handle * n_c)()
+    st = Stats()
+    bv = None if B_values is None else np.ascontiguousarray(B_values, dtype=np.float64)
+    bp = None if B_pts is None else _handles(B_pts)
+    _check(lib().spfhe_sparse_matmul_ct_pt_grouped(ctx, keys, ctypes.byref(A), _handles(A_chunks), len(A_chunks),
+                                                   ctypes.byref(B), _dbl(bv), bp, 1 if merge_digits else 0, outs,
+                                                   n_c, ctypes.byref(st)))
     return [handle(outs[i]) for i in range(n_c)], st.as_dict()

@@ -1,8 +1,10 @@
-"""GPU parity of the lazy-accumulation variant (spfhe_sparse_matmul_ct_ct_grouped)
-against the oracle's spmspm_ct_ct_grouped: result ciphertexts bit-exact on
-identical keys, noise, operands and mask, with and without the digit-by-digit
-rotation merge; op counts equal to the oracle's; decrypted results within
-1e-4 of the FP64 product; error cases."""
+"""GPU parity of the lazy-accumulation variants (spfhe_sparse_matmul_ct_ct_grouped,
+spfhe_sparse_matmul_ct_pt_grouped) against the oracle's spmspm_ct_ct_grouped
+and spmspm_ct_pt_grouped: result ciphertexts bit-exact on identical keys,
+noise, operands, masks and weight plaintexts, with and without the
+digit-by-digit rotation merge, at several batch sizes (the streaming tree
+flushes differently); op counts equal to the oracle's; decrypted results
+within 1e-4 of the FP64 product; error cases."""
 import numpy as np
 import pytest
 
@@ -127,3 +129,68 @@ def _ntt_key(p, k):
         for b in range(2):
             out[j, b] = p.o.rns_ntt(k[j, b], mi)
     return out
+
+
+# ---- streaming tree with many digits, small batches ------------------------
+@pytest.mark.parametrize("batch", [1, 3])
+def test_grouped_base2_streaming_tree(batch):
+    """Base 2 on 64 slots (six digit levels) with one or three groups per
+    batch: tree sums complete and flush at every level while groups stream
+    in; still bit-exact."""
+    case = synthetic.tiny_case(12, 8, 0.3, log_n=7, L=5, dnum=1, rot_base=2)
+    p = _setup(case, rot_base=2)
+    try:
+        p.spfhe.spfhe_ctx_set_match_batch(p.ctx, batch)
+        want, outs, stats, counts = _run_grouped(p, True)
+        for h, w in zip(outs, want):
+            p.assert_ct_equal(h, w)
+        assert stats["ks_final"] == counts.ks_final
+    finally:
+        p.close()
+
+
+# ---- ct x pt ------------------------------------------------------------------
+PT_CASES = {
+    "rect_4x6x5_b2": lambda: synthetic.tiny_case(6, 0, 0.5, log_n=6, rows=4, inner=6, cols=5, rot_base=2),
+    "multi_chunk_8x8_b4": lambda: synthetic.tiny_case(4, 8, 0.35, log_n=6, rot_base=4),
+    "dense_6x9x4_b8": lambda: synthetic.tiny_case(7, 0, 0.0, log_n=6, rows=6, inner=9, cols=4, rot_base=8),
+}
+
+
+@pytest.mark.parametrize("batch", [0, 2])
+@pytest.mark.parametrize("merge", [True, False])
+@pytest.mark.parametrize("name", list(PT_CASES))
+def test_ct_pt_grouped_bit_exact(name, merge, batch):
+    case = PT_CASES[name]()
+    p = _setup(case, rot_base=case.ring.rot_base)
+    try:
+        o, P, sp = p.o, p.P, p.spfhe
+        if batch:
+            sp.spfhe_ctx_set_match_batch(p.ctx, batch)
+        Bd = p.Bcsc[2]
+        base = [o.encode_onehot(float(v), 0, P.L, spmspm.weight_scale(o)) for v in Bd]
+        counts = spmspm.OpCounts()
+        want = spmspm.spmspm_ct_pt_grouped(o, p.keys, p.Acsr[:2], p.A_cts, p.Bcsc[:2], Bd, p.rows, p.cols,
+                                           b_pts=base, merge_digits=merge, counts=counts)
+        gA = [p.import_ct(c) for c in p.A_cts]
+        gpts = [p.import_pt(b) for b in base]
+        outs, stats = sp.spfhe_sparse_matmul_ct_pt_grouped(p.ctx, p.gkeys, p.Am, gA, p.Bm, None, gpts, p.n_c,
+                                                           merge_digits=merge)
+        assert len(outs) == len(want)
+        for h, w in zip(outs, want):
+            p.track("ct", h)
+            p.assert_ct_equal(h, w)
+        for k in ("matches", "ks_final", "rescales"):
+            assert stats[k] == getattr(counts, k), k
+        C = spmspm.decrypt_result(o, p.keys, want, p.rows, p.cols)
+        assert np.max(np.abs(C - spmspm.matmul_fp64(case.A, case.B))) < 1e-4
+        # the library's own weight encoding: the same product within tolerance
+        outs2, _ = sp.spfhe_sparse_matmul_ct_pt_grouped(p.ctx, p.gkeys, p.Am, gA, p.Bm, Bd, None, p.n_c)
+        vals = []
+        for h in outs2:
+            pt = p.track("pt", sp.spfhe_decrypt(p.ctx, p.gkeys, p.track("ct", h)))
+            vals.append(sp.spfhe_decode(p.ctx, pt, P.slots).real)
+        got = np.concatenate(vals)[: p.rows * p.cols].reshape(p.rows, p.cols)
+        assert np.max(np.abs(got - spmspm.matmul_fp64(case.A, case.B))) < 1e-4
+    finally:
+        p.close()

@@ -149,6 +149,12 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * Results do not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
+/* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
+ * the rescale's spread and last step run inside the forward transforms that
+ * feed them (kernel variant 0, n >= 2^12); 0: as separate kernels.  Results
+ * do not depend on it. */
+spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable);
+
 /* Number of kernels the library has launched since the context was created. */
 uint64_t spfhe_launch_count(const spfhe_ctx *ctx);
 

@@ -183,6 +183,14 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages)
     });
 }
 
+spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        ctx->c.fuse_epilogues = enable != 0;
+    });
+}
+
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {

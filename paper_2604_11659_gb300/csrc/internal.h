@@ -108,6 +108,7 @@ struct Ctx {
     int ntt_chunk = 0;               // limbs per pass-A/pass-B launch pair (0: whole batch)
     int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
     int ntt_variant = 0;             // radix-16 kernel variant (0, 1, 2)
+    bool fuse_epilogues = true;      // ModDown / rescale epilogues inside the forward transform
 };
 
 struct Keys {

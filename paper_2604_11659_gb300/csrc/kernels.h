@@ -16,6 +16,29 @@ struct Batch {
 // ---- NTT (ntt.cu) ----
 // Forward / inverse negacyclic NTT of the limbs `map` names in every item.
 void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map);
+
+// Forward transforms with a fused prologue or epilogue (radix-16 sizes,
+// kernel variant 0, no item list; returns false otherwise and does nothing):
+//   kFuseModDown: the transform of ModDown's conv [items][2][ell][n] writes
+//     out = base[sigma(k)] + (acc - conv) P^{-1} instead of conv;
+//   kFuseRescale: pass A reads [r]_{q_i} from the centred top limbs
+//     (top [items][polys][n]) instead of a spread buffer, pass B writes
+//     out = (in - [r]_{q_i}) q_t^{-1}; the batch is the spread buffer
+//     [items][polys][ell-1][n] that holds the intermediate pass.
+enum { kFuseNone = 0, kFuseModDown = 1, kFuseRescale = 2 };
+struct FuseArgs {
+    int ell = 0, K = 0, polys = 0, base_c1 = 0;
+    const u64 *acc = nullptr;
+    long long acc_stride = 0, out_stride = 0;
+    const u64 *const *base = nullptr;
+    const int *base_g = nullptr;
+    u64 *out = nullptr;
+    const u64 *pinv = nullptr, *pinvp = nullptr;
+    const u64 *top = nullptr;
+    const u64 *const *in = nullptr;
+    const u64 *qt_mod = nullptr, *inv = nullptr, *invp = nullptr;
+};
+bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f);
 void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map);
 LimbMap limb_range(int first_off, int count, int first_mi);
 

@@ -205,3 +205,12 @@ __device__ __forceinline__ unsigned brev_bits(unsigned x, int bits)
 {
     return __brev(x) >> (32 - bits);
 }
+
+// Evaluation-domain automorphism X -> X^g: output slot k reads input slot
+// perm_index(k, g) (slot k holds the value at psi^(2 brv(k) + 1)).
+__device__ __forceinline__ int perm_index(int k, unsigned g, int log_n)
+{
+    const unsigned e = 2u * brev_bits((unsigned)k, log_n) + 1u;
+    const unsigned e2 = (e * g) & ((2u << log_n) - 1u);
+    return (int)brev_bits((e2 - 1u) >> 1, log_n);
+}

@@ -375,8 +375,9 @@ __device__ __forceinline__ void r16_prefetch_wait()
     __syncthreads();
 }
 
-template <int P, bool LAZY>
-__device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n)
+template <int P, bool LAZY, int MODE>
+__device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n,
+                                             const FuseArgs &f, const ModConst *__restrict__ mc)
 {
     constexpr int TPC = kElems >> P;   // columns per CTA
     constexpr int R = (P + 3) / 4;
@@ -384,8 +385,24 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
     u64 v[16];
+    if constexpr (MODE == kFuseRescale) {
+        // the limb [r]_{q_i} of the centred top limb r, read from the top limb itself
+        const int slot = blockIdx.y, it = blockIdx.z;
+        const int b = slot / (f.ell - 1), i = slot % (f.ell - 1);
+        const u64 *top = f.top + ((size_t)it * f.polys + b) * ((size_t)1 << log_n);
+        const ModConst m = mc[i];
+        const u64 qt_half = mc[f.ell - 1].q >> 1, qt_mod = __ldg(f.qt_mod + i);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
+        for (int x = 0; x < 16; ++x) {
+            const u64 c = top[((size_t)r16_index<P, 0>(t, x) << lg_ncols) + gcol];
+            u64 r = mul_shoup(redc(U128{c, 0}, m.q, m.qneg_inv), m.r_mod, m.r_mod_p, m.q);
+            if (c > qt_half) r = sub_mod(r, qt_mod, m.q);
+            v[x] = r;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
+    }
     r16_fwd_round<P, 0, LAZY>(v, t, w2, q, 0, 0);
     if constexpr (R > 1) {
 #pragma unroll
@@ -408,9 +425,10 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
     for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
 }
 
-template <int P, int V>
+template <int P, int V, int MODE = kFuseNone>
 __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a, const ModConst *__restrict__ mc,
-                                                                      const ulonglong2 *__restrict__ tw2, int log_n)
+                                                                      const ulonglong2 *__restrict__ tw2, int log_n,
+                                                                      FuseArgs f)
 {
     __shared__ u64 sm[r16_smem_words_a<P>()];
     const int n = 1 << log_n;
@@ -418,13 +436,14 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
-    if (q < kLazyFwdBound) fwd16_a_body<P, true>(sm, p, q, w2, log_n);
-    else fwd16_a_body<P, false>(sm, p, q, w2, log_n);
+    if (q < kLazyFwdBound) fwd16_a_body<P, true, MODE>(sm, p, q, w2, log_n, f, mc);
+    else fwd16_a_body<P, false, MODE>(sm, p, q, w2, log_n, f, mc);
 }
 
-template <int P, bool LAZY, bool SM>
+template <int P, bool LAZY, bool SM, int MODE = kFuseNone>
 __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m, const ulonglong2 *__restrict__ w2,
-                                             int PA, const ulonglong2 *smt)
+                                             int PA, const ulonglong2 *smt, const FuseArgs &f = FuseArgs{},
+                                             int log_n = 0)
 {
     constexpr int TPT = 1 << (P - 4);  // threads per tile
     constexpr int R = (P + 3) / 4;
@@ -461,16 +480,48 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
 #pragma unroll
     for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
     __syncthreads();
-    for (int x = threadIdx.x; x < kElems; x += 256) {
-        const u64 y = sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))];
-        p[e0 + x] = reduce_any(y, q, m.one_p);
+    if constexpr (MODE == kFuseNone) {
+        for (int x = threadIdx.x; x < kElems; x += 256) {
+            const u64 y = sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))];
+            p[e0 + x] = reduce_any(y, q, m.one_p);
+        }
+    } else if constexpr (MODE == kFuseModDown) {
+        // out_b[i] = base_b[sigma(k)] + (acc_b[i] - conv_b[i]) P^{-1} (conv = this transform)
+        const int slot = blockIdx.y, it = blockIdx.z;
+        const int b = slot / f.ell, i = slot % f.ell;
+        const int next = f.ell + f.K;
+        const u64 pinv = __ldg(f.pinv + i), pinvp = __ldg(f.pinvp + i);
+        const u64 *acc = f.acc + it * f.acc_stride + ((size_t)b * next + i) * ((size_t)1 << log_n);
+        const bool add_base = f.base && (b == 0 || f.base_c1);
+        const u64 *base = add_base ? f.base[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n) : nullptr;
+        const unsigned g = f.base_g ? (unsigned)f.base_g[it] : 1u;
+        u64 *out = f.out + it * f.out_stride + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+        for (int x = threadIdx.x; x < kElems; x += 256) {
+            const size_t k = e0 + x;
+            const u64 c = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+            u64 v = mul_shoup(sub_mod(acc[k], c, q), pinv, pinvp, q);
+            if (add_base) v = add_mod(v, base[f.base_g ? perm_index((int)k, g, log_n) : (int)k], q);
+            out[k] = v;
+        }
+    } else {
+        // rescale: out_b[i] = (in_b[i] - [r]_{q_i}) q_t^{-1} ([r]_{q_i} = this transform)
+        const int slot = blockIdx.y, it = blockIdx.z;
+        const int b = slot / (f.ell - 1), i = slot % (f.ell - 1);
+        const u64 inv = __ldg(f.inv + i), invp = __ldg(f.invp + i);
+        const u64 *in = f.in[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+        u64 *out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
+        for (int x = threadIdx.x; x < kElems; x += 256) {
+            const size_t k = e0 + x;
+            const u64 r = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+            out[k] = mul_shoup(sub_mod(in[k], r, q), inv, invp, q);
+        }
     }
 }
 
-template <int P, int V>
+template <int P, int V, int MODE = kFuseNone>
 __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a, const ModConst *__restrict__ mc,
                                                                       const ulonglong2 *__restrict__ tw2, int log_n,
-                                                                      int PA)
+                                                                      int PA, FuseArgs f)
 {
     __shared__ u64 sm[r16_smem_words_b<P>()];
     extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
@@ -479,7 +530,10 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
-    if constexpr (V == 2) {
+    if constexpr (MODE != kFuseNone) {
+        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, MODE>(sm, p, m, w2, PA, nullptr, f, log_n);
+        else fwd16_b_body<P, false, false, MODE>(sm, p, m, w2, PA, nullptr, f, log_n);
+    } else if constexpr (V == 2) {
         r16_prefetch_tw<P>(smt, w2, PA, (int)(((size_t)blockIdx.x * kElems) >> P));
         if (m.q < kLazyFwdBound) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
         else fwd16_b_body<P, false, true>(sm, p, m, w2, PA, smt);
@@ -601,12 +655,12 @@ template <int P, int V, int DIR, typename K> size_t r16_b_smem(K kernel)
 template <int P, int V> struct R16LaunchV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
-        k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n);
+        k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, FuseArgs{});
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA)
     {
         const size_t smem = r16_b_smem<P, V, 0>(k_fwd16_b<P, V>);
-        k_fwd16_b<P, V><<<g, 256, smem, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA);
+        k_fwd16_b<P, V><<<g, 256, smem, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, FuseArgs{});
     }
     static void inv_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c)
     {
@@ -616,6 +670,20 @@ template <int P, int V> struct R16LaunchV {
     {
         const size_t smem = r16_b_smem<P, V, 1>(k_inv16_b<P, V>);
         k_inv16_b<P, V><<<g, 256, smem, s>>>(a, c.dt.mc, c.dt.itw2, c.log_n, PA);
+    }
+};
+
+// transforms with a fused prologue / epilogue (kernel variant 0)
+template <int P> struct R16Fused {
+    static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
+    {
+        if (mode == kFuseRescale) k_fwd16_a<P, 0, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+        else k_fwd16_a<P, 0><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+    }
+    static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
+    {
+        if (mode == kFuseRescale) k_fwd16_b<P, 0, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+        else k_fwd16_b<P, 0, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
     }
 };
 
@@ -646,6 +714,17 @@ template <int P> struct R16Launch {
         variant(c.ntt_variant, [&](auto L) { decltype(L)::inv_b(g, s, a, c, PA); });
     }
 };
+
+template <typename F> void r16_fused_dispatch(int P, F &&f)
+{
+    switch (P) {
+    case 6: f(R16Fused<6>{}); break;
+    case 7: f(R16Fused<7>{}); break;
+    case 8: f(R16Fused<8>{}); break;
+    case 9: f(R16Fused<9>{}); break;
+    default: throw Error(SPFHE_EINVAL, "no radix-16 pass for this size");
+    }
+}
 
 template <typename F> void r16_dispatch(int P, F &&f)
 {
@@ -772,6 +851,31 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
         k_fwd_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA, g.lgE);
         prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
     }
+}
+
+bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f)
+{
+    if (ctx.log_n < 12 || ctx.ntt_variant != 0 || b.ids) return false;
+    launch_checks(b, map);
+    if (map.nl <= 0 || b.items <= 0) return true;
+    NttArgs a{b.base, b.stride, b.ids, map};
+    const int cls = ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD;
+    const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
+    dim3 grid(ctx.n / kElems, map.nl, b.items);
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        r16_fused_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, a, ctx, mode, f); });
+        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items,
+                 mode == kFuseRescale ? "ntt fwd A + rescale spread" : "ntt fwd A");
+    }
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        r16_fused_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, a, ctx, PA, mode, f); });
+        prof_end(ctx, t0_, cls, (mode == kFuseModDown ? 40.0 : 32.0) * ctx.n * map.nl * b.items,
+                 0.5 * ctx.n * PB * map.nl * b.items,
+                 mode == kFuseRescale ? "ntt fwd B + rescale final" : "ntt fwd B + moddown final");
+    }
+    return true;
 }
 
 void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)

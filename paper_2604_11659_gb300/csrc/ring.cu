@@ -13,14 +13,6 @@ constexpr int kT = 256;
 
 inline dim3 grid_n(int n, int y, int z) { return dim3((n + kT - 1) / kT, y, z); }
 
-// out index permutation of sigma_g in evaluation representation:
-// out[k] = in[k'], 2 brv(k') + 1 = g (2 brv(k) + 1) mod 2n.
-__device__ __forceinline__ int perm_index(int k, unsigned g, int log_n)
-{
-    const unsigned e = 2u * brev_bits((unsigned)k, log_n) + 1u;
-    const unsigned e2 = (e * g) & ((2u << log_n) - 1u);
-    return (int)brev_bits((e2 - 1u) >> 1, log_n);
-}
 
 __global__ void k_tensor(int ell, int n, const u64 *const *pa, const u64 *const *pb, u64 *d,
                          const ModConst *__restrict__ mc)
@@ -725,6 +717,21 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
             qm.off[b * ell + i] = b * ell + i;
             qm.mi[b * ell + i] = i;
         }
+    // the transform of conv writes ModDown's output directly where it can
+    FuseArgs fa;
+    fa.ell = ell;
+    fa.K = ctx.K;
+    fa.acc = acc;
+    fa.acc_stride = acc_stride;
+    fa.base = base;
+    fa.base_g = base_g;
+    fa.base_c1 = base_c1 ? 1 : 0;
+    fa.out = out;
+    fa.out_stride = out_stride;
+    fa.pinv = ctx.dt.md_pinv;
+    fa.pinvp = ctx.dt.md_pinv_p;
+    if (ctx.fuse_epilogues && ntt_forward_fused(ctx, Batch{conv, 2LL * ell * ctx.n, items, nullptr}, qm, kFuseModDown, fa))
+        return;
     ntt_forward(ctx, Batch{conv, 2LL * ell * ctx.n, items, nullptr}, qm);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
@@ -755,12 +762,6 @@ void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *
         tm.mi[b] = ell - 1;
     }
     ntt_inverse(ctx, Batch{top, (long long)polys * n, items, nullptr}, tm);
-    {
-        cudaEvent_t t0_ = prof_begin(ctx);
-        k_rescale_spread<<<grid_n(n, polys * (ell - 1), items), kT, 0, ctx.stream>>>(
-            polys, ell, n, top, spread, ctx.dt.mc, ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L);
-        prof_end(ctx, t0_, K_RESCALE, 8.0 * n * items * polys * ell, 1.0 * n * items * polys * (ell - 1), "rescale spread");
-    }
     LimbMap sm;
     sm.nl = polys * (ell - 1);
     for (int b = 0; b < polys; ++b)
@@ -768,6 +769,26 @@ void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *
             sm.off[b * (ell - 1) + i] = b * (ell - 1) + i;
             sm.mi[b * (ell - 1) + i] = i;
         }
+    // the transform reads the top limbs and writes the rescaled output where it can
+    FuseArgs fa;
+    fa.ell = ell;
+    fa.polys = polys;
+    fa.top = top;
+    fa.in = in;
+    fa.out = out;
+    fa.out_stride = out_stride;
+    fa.qt_mod = ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L;
+    fa.inv = ctx.dt.rs_inv + (size_t)(ell - 1) * ctx.L;
+    fa.invp = ctx.dt.rs_inv_p + (size_t)(ell - 1) * ctx.L;
+    if (ctx.fuse_epilogues && ell >= 2 &&
+        ntt_forward_fused(ctx, Batch{spread, (long long)polys * (ell - 1) * n, items, nullptr}, sm, kFuseRescale, fa))
+        return;
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_rescale_spread<<<grid_n(n, polys * (ell - 1), items), kT, 0, ctx.stream>>>(
+            polys, ell, n, top, spread, ctx.dt.mc, ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L);
+        prof_end(ctx, t0_, K_RESCALE, 8.0 * n * items * polys * ell, 1.0 * n * items * polys * (ell - 1), "rescale spread");
+    }
     ntt_forward(ctx, Batch{spread, (long long)polys * (ell - 1) * n, items, nullptr}, sm);
     {
         cudaEvent_t t0_ = prof_begin(ctx);

@@ -65,6 +65,7 @@ _SIGS = [
     ("spfhe_ctx_set_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_ctx_set_ntt_split", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_ctx_set_ntt_variant", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_ctx_set_fusion", ctypes.c_int, [handle, ctypes.c_int]),
     ("spfhe_tune_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32), c_dblp]),
@@ -227,6 +228,10 @@ def spfhe_ctx_set_ntt_chunk(ctx, limbs: int):
 
 def spfhe_ctx_set_ntt_split(ctx, pass_a_stages: int):
     _check(lib().spfhe_ctx_set_ntt_split(ctx, int(pass_a_stages)))
+
+
+def spfhe_ctx_set_fusion(ctx, enable: bool):
+    _check(lib().spfhe_ctx_set_fusion(ctx, 1 if enable else 0))
 
 
 def spfhe_ctx_set_ntt_variant(ctx, variant: int):

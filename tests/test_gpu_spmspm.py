@@ -169,3 +169,18 @@ def _ntt_key(p, k):
         for b in range(2):
             out[j, b] = p.o.rns_ntt(k[j, b], mi)
     return out
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_ct_ct_fusion_on_off_bit_exact(fused):
+    """ModDown and rescale epilogues inside the forward transforms or as
+    separate kernels: the same bits (n = 2^12 takes the radix-16 path)."""
+    case = synthetic.case_16x16(seed=0)
+    p = _setup(case)
+    try:
+        p.spfhe.spfhe_ctx_set_fusion(p.ctx, fused)
+        want, outs, stats, counts = _run_ct_ct(p)
+        for h, w in zip(outs, want):
+            p.assert_ct_equal(h, w)
+    finally:
+        p.close()

@@ -145,13 +145,14 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * read per butterfly stage from global memory at 3 CTAs per SM; 1 = the same
  * with the register budget of 2 CTAs per SM; 2 = as 1, with the second pass
  * copying its twiddles into shared memory asynchronously before its data
- * loads (about 64 KB of dynamic shared memory per CTA).  EINVAL otherwise.
+ * loads (about 64 KB of dynamic shared memory per CTA); 3 = as 0 with the
+ * register budget of 4 CTAs per SM.  EINVAL otherwise.
  * Results do not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
 /* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
  * the rescale's spread and last step run inside the forward transforms that
- * feed them (kernel variant 0, n >= 2^12); 0: as separate kernels.  Results
+ * feed them (kernel variant 0 or 3, n >= 2^12); 0: as separate kernels.  Results
  * do not depend on it. */
 spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable);
 

@@ -283,15 +283,22 @@ __device__ __forceinline__ void r16_fwd_stage(u64 (&v)[16], int t, const ulonglo
     }
 }
 
-template <int P, int RND, int l, bool SM>
+// PRE: the stage's twiddles were loaded ahead into `pre`
+template <int P, int RND, int l, bool SM, bool PRE = false>
 __device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
-                                              int stage0, int btile, const ulonglong2 *smt, int ltile)
+                                              int stage0, int btile, const ulonglong2 *smt, int ltile,
+                                              const ulonglong2 (*pre)[16] = nullptr)
 {
     constexpr int Q = r16_q<P, RND>();
     constexpr int half = 1 << (Q - 1 - l);
     const u64 q3 = 3 * q, nq = 0 - q;
     ulonglong2 wt[16];
-    r16_load_tw<P, RND, Q, l, SM>(wt, t, w2, stage0, btile, smt, ltile);
+    if constexpr (PRE) {
+#pragma unroll
+        for (int g = 0; g < (16 >> (Q - l)); ++g) wt[g] = (*pre)[g];
+    } else {
+        r16_load_tw<P, RND, Q, l, SM>(wt, t, w2, stage0, btile, smt, ltile);
+    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (i & half) continue;
@@ -320,16 +327,17 @@ __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const ulonglo
 // moduli below this take the reduction-free forward butterflies
 constexpr u64 kLazyFwdBound = 1ull << 58;
 
-template <int P, int RND, bool SM = false>
+// PRE: the twiddles of the round's first stage (l = Q - 1) are in `pre`
+template <int P, int RND, bool SM = false, bool PRE = false>
 __device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt = nullptr,
-                                              int ltile = 0)
+                                              int ltile = 0, const ulonglong2 (*pre)[16] = nullptr)
 {
     constexpr int Q = r16_q<P, RND>();
-    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    r16_inv_stage<P, RND, 0, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM, PRE>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM, PRE && Q == 3>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM, PRE && Q == 2>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    r16_inv_stage<P, RND, 0, SM, PRE && Q == 1>(v, t, w2, q, stage0, btile, smt, ltile, pre);
 }
 
 // shared-memory slot of tile element j (pass B layout; pad one word per 16)
@@ -350,7 +358,7 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 //   1: the same with the register budget of 2 CTAs per SM;
 //   2: as 1, and pass B copies its CTA's twiddles into shared memory with
 //      asynchronous copies issued before its data loads.
-template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : 2; }
+template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V == 3 ? 4 : 2); }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -561,14 +569,19 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
     const size_t e0 = (size_t)blockIdx.x * kElems;
     const int btile = (int)(e0 >> P) + tile;
+    // the first stage's twiddles are requested before the data, so their
+    // latency overlaps the data loads
+    constexpr int Q1 = r16_q<P, R - 1>();
+    ulonglong2 wpre[16];
     if constexpr (SM) r16_prefetch_tw<P>(smt, w2, PA, (int)(e0 >> P));
+    else r16_load_tw<P, R - 1, Q1, Q1 - 1, false>(wpre, t, w2, PA, btile, nullptr, 0);
     for (int x = threadIdx.x; x < kElems; x += 256) sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = p[e0 + x];
     if constexpr (SM) r16_prefetch_wait();
     else __syncthreads();
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
-    r16_inv_round<P, R - 1, SM>(v, t, w2, q, PA, btile, smt, tile);
+    r16_inv_round<P, R - 1, SM, !SM>(v, t, w2, q, PA, btile, smt, tile, &wpre);
     if constexpr (R > 2) {
         __syncthreads();
 #pragma unroll
@@ -673,17 +686,29 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variant 0)
-template <int P> struct R16Fused {
+// transforms with a fused prologue / epilogue (kernel variants 0 and 3)
+template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
-        if (mode == kFuseRescale) k_fwd16_a<P, 0, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
-        else k_fwd16_a<P, 0><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+        if (mode == kFuseRescale) k_fwd16_a<P, V, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+        else k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
-        if (mode == kFuseRescale) k_fwd16_b<P, 0, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
-        else k_fwd16_b<P, 0, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+        if (mode == kFuseRescale) k_fwd16_b<P, V, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+        else k_fwd16_b<P, V, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+    }
+};
+template <int P> struct R16Fused {
+    static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
+    {
+        if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
+        else R16FusedV<P, 0>::fwd_a(g, s, a, c, mode, f);
+    }
+    static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
+    {
+        if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
+        else R16FusedV<P, 0>::fwd_b(g, s, a, c, PA, mode, f);
     }
 };
 
@@ -694,6 +719,7 @@ template <int P> struct R16Launch {
         case 0: f(R16LaunchV<P, 0>{}); break;
         case 1: f(R16LaunchV<P, 1>{}); break;
         case 2: f(R16LaunchV<P, 2>{}); break;
+        case 3: f(R16LaunchV<P, 3>{}); break;
         default: throw Error(SPFHE_EINVAL, "no such NTT variant");
         }
     }
@@ -855,7 +881,7 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
 
 bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f)
 {
-    if (ctx.log_n < 12 || ctx.ntt_variant != 0 || b.ids) return false;
+    if (ctx.log_n < 12 || (ctx.ntt_variant != 0 && ctx.ntt_variant != 3) || b.ids) return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
     NttArgs a{b.base, b.stride, b.ids, map};

@@ -171,14 +171,15 @@ def _ntt_key(p, k):
     return out
 
 
-@pytest.mark.parametrize("fused", [True, False])
-def test_ct_ct_fusion_on_off_bit_exact(fused):
+@pytest.mark.parametrize("fused,variant", [(True, 0), (True, 3), (False, 0)])
+def test_ct_ct_fusion_on_off_bit_exact(fused, variant):
     """ModDown and rescale epilogues inside the forward transforms or as
     separate kernels: the same bits (n = 2^12 takes the radix-16 path)."""
     case = synthetic.case_16x16(seed=0)
     p = _setup(case)
     try:
         p.spfhe.spfhe_ctx_set_fusion(p.ctx, fused)
+        p.spfhe.spfhe_ctx_set_ntt_variant(p.ctx, variant)
         want, outs, stats, counts = _run_ct_ct(p)
         for h, w in zip(outs, want):
             p.assert_ct_equal(h, w)

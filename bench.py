@@ -136,15 +136,15 @@ def to_csr(M):
 NTT_CHUNKS = (0, 64, 128, 256, 512)
 
 
-def tune_ntt(sp, ctx, rec, chunk):
-    """chunk >= 0: set it (default split and kernel variant); -1: for every
+def tune_ntt(sp, ctx, rec, chunk, variant=0):
+    """chunk >= 0: set it (default split, kernel `variant`); -1: for every
     kernel variant and split of the two-pass NTT into pass A / pass B stages,
     time the launch-chunk candidates on one match batch of key switches at the
     top level, and keep the fastest.  Returns ((variant, split, chunk),
     timings keyed "variant/split/chunk")."""
     if chunk >= 0:
-        sp.spfhe_ctx_set_ntt_chunk(ctx, chunk)
-        return (0, 0, chunk), None
+        set_ntt(sp, ctx, (variant, 0, chunk))
+        return (variant, 0, chunk), None
     items = 32 if rec.log_n >= 15 else 64
     splits = [pa for pa in range(6, 10) if 6 <= rec.log_n - pa <= 9] if rec.log_n >= 12 else [0]
     best, timings = None, {}
@@ -171,7 +171,7 @@ def set_ntt(sp, ctx, cfg):
 class GpuMatmul:
     """Keys, encrypted operands and the matmul call for one workload."""
 
-    def __init__(self, case, rot_base, stream, ntt_chunk=-1):
+    def __init__(self, case, rot_base, stream, ntt_chunk=-1, ntt_variant=0):
         from paper_2604_11659_gb300 import params as gparams
         from paper_2604_11659_gb300 import spfhe
         self.sp = spfhe
@@ -181,7 +181,7 @@ class GpuMatmul:
         self.gp = gparams.ctx_params(rec, rot_base=rot_base)
         self.K = self.gp.K
         self.ctx = spfhe.spfhe_ctx_create(self.gp, stream)
-        self.ntt_chunk, self.ntt_tune = tune_ntt(spfhe, self.ctx, rec, ntt_chunk)
+        self.ntt_chunk, self.ntt_tune = tune_ntt(spfhe, self.ctx, rec, ntt_chunk, ntt_variant)
         self.n = 1 << rec.log_n
         self.S = self.n // 2
         t = time.time()
@@ -570,7 +570,8 @@ def run_small_case(args):
     A = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
     B = synthetic.bernoulli_sparse(rng, 128, 128, 0.995)
     case = synthetic.MatmulCase("small", A, B, synthetic.ring_128x128())
-    g = GpuMatmul(case, 2, torch.cuda.current_stream().cuda_stream, ntt_chunk=args.ntt_chunk)
+    g = GpuMatmul(case, 2, torch.cuda.current_stream().cuda_stream, ntt_chunk=args.ntt_chunk,
+                  ntt_variant=args.ntt_variant)
     g.sp.spfhe_ctx_set_match_batch(g.ctx, args.small_batch)
     # the product alone sits in an NVTX range "product" (ncu --nvtx-include)
     try:
@@ -601,6 +602,8 @@ def main():
     ap.add_argument("--batch-products", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--graph-steps", type=int, default=2,
+                    help="timed launches of the headline product captured as one CUDA graph (0: skip)")
     ap.add_argument("--dense-layer", type=int, default=1,
                     help="1: run the N=2^17 dense-layer ct x pt product once (lazy accumulation)")
     ap.add_argument("--grouped-steps", type=int, default=2,
@@ -608,6 +611,7 @@ def main():
     ap.add_argument("--ntt-chunk", type=int, default=-1,
                     help="limbs per NTT launch pair; -1 = autotune on the workload's key-switch shape")
     ap.add_argument("--small-batch", type=int, default=8)
+    ap.add_argument("--ntt-variant", type=int, default=0, help="NTT kernel variant when --ntt-chunk is given")
     ap.add_argument("--small-case", action="store_true",
                     help="profiler case: three relinearised products (tensor + key switch) at the workload's ring")
     args = ap.parse_args()
@@ -707,6 +711,31 @@ def main():
         e2e_s = float(t.item())
     e2e_val = world / e2e_s
 
+    # the same product captured once as a CUDA graph, then launched as one unit
+    graph = None
+    if args.graph_steps > 0:
+        t0 = time.time()
+        gr = sp.spfhe_matmul_graph_create(g.ctx, sp.matmul_req(g.keys, g.Am, g.A_cts, g.Bm, g.B_cts), 0)
+        create_s = time.time() - t0
+        sp.spfhe_matmul_graph_launch(gr)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record()
+        for _ in range(args.graph_steps):
+            sp.spfhe_matmul_graph_launch(gr)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms_gr = ev0.elapsed_time(ev1) / args.graph_steps
+        outs, st_gr = sp.spfhe_matmul_graph_results(gr, g.n_c)
+        err_gr = g.check(outs)
+        for h in outs:
+            sp.spfhe_ct_free(h)
+        sp.spfhe_matmul_graph_free(gr)
+        graph = {"what": "the headline product (Alg. 2) captured once as one CUDA graph (%d kernels), launched "
+                         "as one unit per step" % st_gr["launches"],
+                 "ms_per_step": ms_gr, "steps": args.graph_steps, "warmup": 1, "capture_s": round(create_s, 2),
+                 "max_abs_err": err_gr, "vs_eager": ms_step / ms_gr}
+
     # the lazy-accumulation reordering of Alg. 2 on the same operands
     # (reported beside the headline, which times Alg. 2 as printed)
     variant = None
@@ -776,7 +805,7 @@ def main():
                        "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},
             "e2e": {"value": e2e_val, "unit": "matmuls/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
-            "max_abs_err": err, "keygen_s": round(g.keygen_s, 2), "variant_grouped": variant,
+            "max_abs_err": err, "keygen_s": round(g.keygen_s, 2), "graph": graph, "variant_grouped": variant,
             "keyswitch": {"polys": ks_calls, "gbs": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9,
                           "frac_of_hbm": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9 / hbm_peak},
             "kernels": kernels}

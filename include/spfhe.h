@@ -231,6 +231,13 @@ spfhe_status spfhe_decrypt(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_c
  * memory; the copy is enqueued on the context stream and export waits for it. */
 spfhe_status spfhe_ct_import(spfhe_ctx *ctx, const uint64_t *limbs, uint32_t level, double scale,
                              spfhe_ct **out);
+
+/* Replace the contents of ct (its level and scale unchanged) with 2 * level *
+ * n words in the layout of spfhe_ct_import, from host or device memory;
+ * asynchronous on the context stream (a host buffer must stay unchanged
+ * until the copy is done).  Lets a captured graph (spfhe_matmul_graph_*)
+ * run on new operands. */
+spfhe_status spfhe_ct_overwrite(spfhe_ctx *ctx, spfhe_ct *ct, const uint64_t *limbs);
 spfhe_status spfhe_ct_export(spfhe_ctx *ctx, const spfhe_ct *ct, uint64_t *limbs);
 spfhe_status spfhe_ct_info(const spfhe_ct *ct, uint32_t *level, double *scale);
 void spfhe_ct_free(spfhe_ct *ct);
@@ -409,7 +416,8 @@ spfhe_status spfhe_sparse_matmul_batch(spfhe_ctx *ctx, size_t n_req, const spfhe
  * threads meanwhile, except through the server calls.  Between waves of
  * work the worker admits submitted requests in arrival order while their
  * result buffers fit hbm_budget_bytes (a request is always admitted when
- * nothing else runs) and mixes their work into the running batches; results
+ * nothing else runs) and mixes their work into the running batches;
+ results
  * are bit-identical to running each request alone.  Operands and keys of a
  * submitted request must stay alive until spfhe_server_wait returns for it;
  * its metadata is copied at submission. */
@@ -424,6 +432,31 @@ spfhe_status spfhe_server_wait(spfhe_server *srv, uint64_t ticket, spfhe_ct **C_
                                spfhe_stats *stats, double *latency_ms);
 /* Finish every submitted request, stop the worker, free unclaimed results. */
 spfhe_status spfhe_server_destroy(spfhe_server *srv);
+
+/* ---- products captured as one CUDA graph --------------------------------- */
+/* A product planned and captured once into a CUDA graph, launched as one unit
+ * (library extension for the batch-launch pattern; the paper has no
+ * counterpart).  variant 0 = spfhe_sparse_matmul_ct_ct (Alg. 2), 1 =
+ * spfhe_sparse_matmul_ct_ct_grouped with merge_digits.  The request's keys,
+ * operand chunks and mask are read at every launch: they must outlive the
+ * graph, and their contents may change between launches (same levels,
+ * scales and sparsity).  The graph owns its device buffers (a workspace set
+ * of its own, every scratch buffer, the result chunks) until
+ * spfhe_matmul_graph_free.  Creation does no arithmetic; it blocks while it
+ * plans and captures.  EINVAL for bad requests or a capture already running
+ * on the context, EKEY/ELEVEL/ESCALE as the product, ENOMEM, ECUDA. */
+typedef struct spfhe_graph spfhe_graph;
+spfhe_status spfhe_matmul_graph_create(spfhe_ctx *ctx, const spfhe_matmul_req *req, int variant,
+                                       spfhe_graph **out);
+/* Enqueue one launch of the graph on the context stream (asynchronous):
+ * zeroes the result chunks and recomputes the product into them. */
+spfhe_status spfhe_matmul_graph_launch(spfhe_graph *g);
+/* Handles of the graph's n_c result chunks (valid after a launch completes)
+ * and the product's counters; spfhe_ct_free on these handles frees only the
+ * handle, the chunks belong to the graph. */
+spfhe_status spfhe_matmul_graph_results(spfhe_graph *g, spfhe_ct **C_chunks, size_t n_c, spfhe_stats *stats);
+/* Wait for the context stream and free the graph and everything it owns. */
+void spfhe_matmul_graph_free(spfhe_graph *g);
 
 #ifdef __cplusplus
 }

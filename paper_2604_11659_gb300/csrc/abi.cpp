@@ -398,6 +398,16 @@ spfhe_status spfhe_ct_import(spfhe_ctx *ctx, const uint64_t *limbs, uint32_t lev
     });
 }
 
+spfhe_status spfhe_ct_overwrite(spfhe_ctx *ctx, spfhe_ct *ct, const uint64_t *limbs)
+{
+    return guard([&] {
+        need(ct && limbs, "null argument");
+        Ctx &c = C(ctx);
+        SPFHE_CHECK_CUDA(cudaMemcpyAsync(ct->c->d, limbs, 2ull * ct->c->level * c.n * sizeof(u64), cudaMemcpyDefault,
+                                         c.stream));
+    });
+}
+
 spfhe_status spfhe_ct_export(spfhe_ctx *ctx, const spfhe_ct *ct, uint64_t *limbs)
 {
     return guard([&] {
@@ -421,7 +431,7 @@ spfhe_status spfhe_ct_info(const spfhe_ct *ct, uint32_t *level, double *scale)
 void spfhe_ct_free(spfhe_ct *ct)
 {
     if (!ct) return;
-    free_ct(ct->c);
+    if (!ct->borrowed) free_ct(ct->c);
     delete ct;
 }
 

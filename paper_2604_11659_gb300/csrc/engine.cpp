@@ -57,7 +57,8 @@ const u64 *Engine::level_mask(int ell)
     std::vector<int> mi(ml);
     for (int i = 0; i < ml; ++i) mi[i] = i;
     to_montgomery(ctx_, m, ml, mi.data(), 1);
-    ctx_.masks[ell] = m;
+    // a mask made while a graph is captured belongs to that graph
+    if (!ctx_.cap) ctx_.masks[ell] = m;
     return m;
 }
 

@@ -456,7 +456,7 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             tree.finish();
             st_final = tree.ks;
         }
-        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx_sync(ctx);
     } catch (...) {
         free_results(ctx, res);
         throw;
@@ -614,7 +614,7 @@ void spmspm_ct_pt_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             tree.finish();
             st_final = tree.ks;
         }
-        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx_sync(ctx);
     } catch (...) {
         free_results(ctx, res);
         throw;

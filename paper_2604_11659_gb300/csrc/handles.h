@@ -10,6 +10,7 @@ struct spfhe_keys {
 };
 struct spfhe_ct {
     spfhe::Ct *c;
+    bool borrowed = false;   // a graph's result: spfhe_ct_free drops only the handle
 };
 struct spfhe_pt {
     spfhe::Pt *p;

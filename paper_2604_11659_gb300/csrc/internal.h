@@ -107,9 +107,29 @@ struct Ctx {
     int match_batch = 0;             // matches per batch (0: default for the ring size)
     int ntt_chunk = 0;               // limbs per pass-A/pass-B launch pair (0: whole batch)
     int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
-    int ntt_variant = 0;             // radix-16 kernel variant (0, 1, 2)
+    int ntt_variant = 0;             // radix-16 kernel variant (0 to 3)
     bool fuse_epilogues = true;      // ModDown / rescale epilogues inside the forward transform
+    // while a CUDA graph is being captured: its own buffers (graph.cpp)
+    struct Capture *cap = nullptr;
 };
+
+// Resources of a graph under capture: every device buffer allocated while
+// capturing (freed with the graph, never earlier: the graph's nodes use them
+// at every launch), the workspaces of the capture, and an append-only
+// pinned/device pair for the metadata uploads (the captured copies read the
+// pinned bytes at every launch).
+struct Capture {
+    std::vector<void *> device;      // allocated while capturing (cudaMalloc)
+    std::vector<void *> deferred;    // pool buffers released while capturing
+    std::vector<void *> host;
+    std::vector<u64 *> ws;           // workspace slot -> buffer
+    std::vector<size_t> ws_words;
+    char *up_host = nullptr, *up_dev = nullptr;
+    size_t up_off = 0, up_cap = 0;
+};
+
+// host-side wait for the context stream; a no-op while a graph is captured
+void ctx_sync(Ctx &ctx);
 
 struct Keys {
     Ctx *ctx = nullptr;

@@ -56,7 +56,7 @@ void sparse_matmul_batch(Ctx &ctx, size_t n_req, const spfhe_matmul_req *reqs, C
     try {
         for (auto &j : jobs) eng.add(&j);
         eng.run_all();
-        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx_sync(ctx);
     } catch (...) {
         for (auto &j : jobs) release_job(ctx, j, true);
         throw;

@@ -167,7 +167,7 @@ void spmspm_ct_ct(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
     try {
         eng.add(&job);
         eng.run_all();
-        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx_sync(ctx);
     } catch (...) {
         release_job(ctx, job, true);
         throw;
@@ -272,7 +272,7 @@ void spmspm_ct_pt(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
                 st.matches += m;
             }
         }
-        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx_sync(ctx);
     } catch (...) {
         for (size_t c = 0; c < nC; ++c)
             if (C[c]) {

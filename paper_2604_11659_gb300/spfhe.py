@@ -110,6 +110,9 @@ _SIGS = [
                                                  ctypes.c_size_t, ctypes.POINTER(SparseMeta), c_dblp,
                                                  ctypes.POINTER(handle), ctypes.POINTER(handle), ctypes.c_size_t,
                                                  ctypes.POINTER(Stats)]),
+    ("spfhe_matmul_graph_launch", ctypes.c_int, [handle]),
+    ("spfhe_ct_overwrite", ctypes.c_int, [handle, handle, ctypes.c_void_p]),
+    ("spfhe_matmul_graph_free", None, [handle]),
     ("spfhe_sparse_matmul_ct_pt_grouped", ctypes.c_int,
      [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
       c_dblp, ctypes.POINTER(handle), ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
@@ -126,6 +129,10 @@ class MatmulReq(ctypes.Structure):
 
 
 _SIGS += [
+    ("spfhe_matmul_graph_create", ctypes.c_int, [handle, ctypes.POINTER(MatmulReq), ctypes.c_int,
+                                                 ctypes.POINTER(handle)]),
+    ("spfhe_matmul_graph_results", ctypes.c_int, [handle, ctypes.POINTER(handle), ctypes.c_size_t,
+                                                  ctypes.POINTER(Stats)]),
     ("spfhe_sparse_matmul_batch", ctypes.c_int, [handle, ctypes.c_size_t, ctypes.POINTER(MatmulReq),
                                                  ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
     ("spfhe_server_create", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
@@ -543,3 +550,32 @@ def spfhe_sparse_matmul_ct_pt_grouped(ctx, keys, A: SparseMeta, A_chunks, B: Spa
                                                    ctypes.byref(B), _dbl(bv), bp, 1 if merge_digits else 0, outs,
                                                    n_c, ctypes.byref(st)))
     return [handle(outs[i]) for i in range(n_c)], st.as_dict()
+
+
+def spfhe_matmul_graph_create(ctx, req, variant: int = 0):
+    out = handle()
+    _check(lib().spfhe_matmul_graph_create(ctx, ctypes.byref(req), int(variant), ctypes.byref(out)))
+    return out
+
+
+def spfhe_matmul_graph_launch(g):
+    _check(lib().spfhe_matmul_graph_launch(g))
+
+
+def spfhe_matmul_graph_results(g, n_c: int):
+    outs = (handle * n_c)()
+    st = Stats()
+    _check(lib().spfhe_matmul_graph_results(g, outs, n_c, ctypes.byref(st)))
+    return [handle(outs[i]) for i in range(n_c)], st.as_dict()
+
+
+def spfhe_matmul_graph_free(g):
+    lib().spfhe_matmul_graph_free(g)
+
+
+def spfhe_ct_overwrite(ctx, ct, limbs):
+    """Copy new limbs ([2][level][n] uint64, host numpy) into ct; waits for
+    the copy (the host buffer may be reused on return)."""
+    a = np.ascontiguousarray(limbs, dtype=np.uint64)
+    _check(lib().spfhe_ct_overwrite(ctx, ct, ctypes.c_void_p(a.ctypes.data)))
+    spfhe_sync(ctx)

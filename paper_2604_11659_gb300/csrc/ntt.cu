@@ -499,29 +499,47 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         const int b = slot / f.ell, i = slot % f.ell;
         const int next = f.ell + f.K;
         const u64 pinv = __ldg(f.pinv + i), pinvp = __ldg(f.pinvp + i);
-        const u64 *acc = f.acc + it * f.acc_stride + ((size_t)b * next + i) * ((size_t)1 << log_n);
+        const u64 *__restrict__ acc = f.acc + it * f.acc_stride + ((size_t)b * next + i) * ((size_t)1 << log_n);
         const bool add_base = f.base && (b == 0 || f.base_c1);
-        const u64 *base = add_base ? f.base[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n) : nullptr;
+        const u64 *__restrict__ base =
+            add_base ? f.base[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n) : nullptr;
         const unsigned g = f.base_g ? (unsigned)f.base_g[it] : 1u;
-        u64 *out = f.out + it * f.out_stride + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
-        for (int x = threadIdx.x; x < kElems; x += 256) {
-            const size_t k = e0 + x;
-            const u64 c = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
-            u64 v = mul_shoup(sub_mod(acc[k], c, q), pinv, pinvp, q);
-            if (add_base) v = add_mod(v, base[f.base_g ? perm_index((int)k, g, log_n) : (int)k], q);
-            out[k] = v;
+        u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+        // eight elements per thread at a time: all their loads in flight together
+        for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+            u64 av[8], bv[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const size_t k = e0 + x0 + r * 256;
+                av[r] = acc[k];
+                bv[r] = add_base ? base[f.base_g ? perm_index((int)k, g, log_n) : (int)k] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int x = x0 + r * 256;
+                const u64 c = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+                u64 v = mul_shoup(sub_mod(av[r], c, q), pinv, pinvp, q);
+                if (add_base) v = add_mod(v, bv[r], q);
+                out[e0 + x] = v;
+            }
         }
     } else {
         // rescale: out_b[i] = (in_b[i] - [r]_{q_i}) q_t^{-1} ([r]_{q_i} = this transform)
         const int slot = blockIdx.y, it = blockIdx.z;
         const int b = slot / (f.ell - 1), i = slot % (f.ell - 1);
         const u64 inv = __ldg(f.inv + i), invp = __ldg(f.invp + i);
-        const u64 *in = f.in[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
-        u64 *out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
-        for (int x = threadIdx.x; x < kElems; x += 256) {
-            const size_t k = e0 + x;
-            const u64 r = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
-            out[k] = mul_shoup(sub_mod(in[k], r, q), inv, invp, q);
+        const u64 *__restrict__ in = f.in[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+        u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
+        for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+            u64 cv[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) cv[r] = in[e0 + x0 + r * 256];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int x = x0 + r * 256;
+                const u64 rr = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+                out[e0 + x] = mul_shoup(sub_mod(cv[r], rr, q), inv, invp, q);
+            }
         }
     }
 }

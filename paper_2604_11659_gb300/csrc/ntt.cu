@@ -593,7 +593,18 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     ulonglong2 wpre[16];
     if constexpr (SM) r16_prefetch_tw<P>(smt, w2, PA, (int)(e0 >> P));
     else r16_load_tw<P, R - 1, Q1, Q1 - 1, false>(wpre, t, w2, PA, btile, nullptr, 0);
-    for (int x = threadIdx.x; x < kElems; x += 256) sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = p[e0 + x];
+    // loads before stores, eight at a time (the stores into shared memory
+    // would otherwise wait for each load in turn)
+    for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+        u64 tmp[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) tmp[r] = p[e0 + x0 + r * 256];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int x = x0 + r * 256;
+            sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = tmp[r];
+        }
+    }
     if constexpr (SM) r16_prefetch_wait();
     else __syncthreads();
     u64 v[16];

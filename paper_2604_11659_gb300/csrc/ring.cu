@@ -121,9 +121,12 @@ __global__ void __launch_bounds__(256, 4) k_modup_bconv(int digit0, int ell, int
     const uint32_t v = (uint32_t)rint(f);
     const int next = ell + K;
     u64 *dst = ext + it * ext_stride + (size_t)j * next * n + k;
-    for (int t = 0; t < lo; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + t * RL, y0, y1, v);
-    for (int t = hi; t < ell; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + t * RL, y0, y1, v);
-    for (int t = ell; t < next; ++t) dst[(size_t)t * n] = bconv_out<NS>(sh + (L + t - ell) * RL, y0, y1, v);
+    // global stores (st.global): the shared-memory constant loads need not
+    // wait for them
+    for (int t = 0; t < lo; ++t) __stcg(dst + (size_t)t * n, bconv_out<NS>(sh + t * RL, y0, y1, v));
+    for (int t = hi; t < ell; ++t) __stcg(dst + (size_t)t * n, bconv_out<NS>(sh + t * RL, y0, y1, v));
+    for (int t = ell; t < next; ++t)
+        __stcg(dst + (size_t)t * n, bconv_out<NS>(sh + (L + t - ell) * RL, y0, y1, v));
 }
 
 // Inner product with the switching key: acc_b[t] = sum_j E_j[t] k_{j,b}[t].
@@ -144,8 +147,9 @@ struct IpGroups {
 // Products are summed carry-free (Acc30) and reduced by one REDC.
 template <int BETA>
 __global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, int M, int n, const u64 *const *in,
-                                            const u64 *ext, long long ext_stride, IpGroups groups, u64 *acc,
-                                            long long acc_stride, const ModConst *__restrict__ mc)
+                                            const u64 *__restrict__ ext, long long ext_stride, IpGroups groups,
+                                            u64 *__restrict__ acc, long long acc_stride,
+                                            const ModConst *__restrict__ mc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(256, 4) k_moddown_bconv(int ell, int L, int M,
     }
     const uint32_t v = (uint32_t)rint(f);
     u64 *dst = conv + ((size_t)it * 2 + b) * ell * n + k;
-    for (int t = 0; t < ell; ++t) dst[(size_t)t * n] = bconv_out<KK>(sh + t * RL, y0, y1, v);
+    for (int t = 0; t < ell; ++t) __stcg(dst + (size_t)t * n, bconv_out<KK>(sh + t * RL, y0, y1, v));
 }
 
 // out_b[i] = base_b[sigma(i)] + (acc_b[i] - conv_b[i]) P^{-1} mod q_i

@@ -101,6 +101,8 @@ def lib():
         L.or_bconv.argtypes = [u64p, u64p, ctypes.c_int, u64p, u64p, ctypes.c_int, ctypes.c_int]
         pp = ctypes.POINTER(_OrParams)
         L.or_keyswitch.argtypes = [pp, u64p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_modup.argtypes = [pp, u64p, ctypes.c_int, u64p]
+        L.or_ks_ext.argtypes = [pp, u64p, ctypes.c_int, u64p, u64, u64p, u64p]
         L.or_rescale.argtypes = [pp, u64p, ctypes.c_int]
         ip = ctypes.POINTER(ctypes.c_int)
         L.or_rns_polymul.argtypes = [pp, u64p, u64p, u64p, ctypes.c_int, ip]
@@ -634,6 +636,40 @@ class Oracle:
         k0, k1 = self.keyswitch(a1, keys.rot[r])
         c0 = np.stack([addmod(a0[i], k0[i], q) for i, q in enumerate(mods)])
         return Ct(c0, k1, ct.scale)
+
+    def modup(self, c: np.ndarray) -> np.ndarray:
+        """ModUp of every digit of c (coefficient domain): [beta][ell+K][n]."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        ell = c.shape[0]
+        beta = -(-ell // self.P.alpha)
+        ext = np.zeros((beta, ell + self.P.K, self.n), dtype=np.uint64)
+        lib().or_modup(ctypes.byref(self._cs), _p(c), ell, _p(ext))
+        return ext
+
+    def rotate_hoisted(self, ct: Ct, amounts: list, keys: Keys) -> list:
+        """Rotations of one ciphertext by several amounts (each with a key of
+        its own) sharing one ModUp of c1: the automorphism is applied to the
+        extended digits, then inner product and ModDown per amount."""
+        ext = self.modup(ct.c1)
+        ell = ct.level
+        mods = self.mods[:ell]
+        out = []
+        for r in amounts:
+            r %= self.P.slots
+            if r == 0:
+                out.append(ct.copy())
+                continue
+            if r not in keys.rot:
+                raise KeyError("no rotation key for %d" % r)
+            g = pow(5, r, 2 * self.n)
+            k0 = np.zeros((ell, self.n), dtype=np.uint64)
+            k1 = np.zeros((ell, self.n), dtype=np.uint64)
+            ksk = np.ascontiguousarray(keys.rot[r], dtype=np.uint64)
+            lib().or_ks_ext(ctypes.byref(self._cs), _p(ext), ell, _p(ksk), g, _p(k0), _p(k1))
+            a0 = np.stack([automorphism(ct.c0[i], g, q) for i, q in enumerate(mods)])
+            c0 = np.stack([addmod(a0[i], k0[i], q) for i, q in enumerate(mods)])
+            out.append(Ct(c0, k1, ct.scale))
+        return out
 
     def rotation_plan(self, r: int) -> list:
         return rotation_plan(r, self.P.slots, self.P.rot_base)

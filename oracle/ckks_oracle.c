@@ -353,43 +353,62 @@ static int ext_mod_index(const or_params *P, int ell, int t) { return t < ell ? 
  *            centred representative (or_bconv_centred), i.e. out_b is
  *            acc_b / P rounded to the nearest integer, coefficient-wise
  * out0, out1: ell limbs each. */
-void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64 *out0, u64 *out1)
+/* ModUp of every digit of c (ell limbs, coefficient domain): ext receives
+ * [beta][ell + K][n], digit j's own limbs copied, every other limb the
+ * centred base conversion of the digit (reading R12). */
+void or_modup(const or_params *P, const u64 *c, int ell, u64 *ext)
 {
     int n = 1 << P->log_n, L = P->L, K = P->K, dnum = P->dnum;
     int alpha = (L + dnum - 1) / dnum;
     int n_ext = ell + K;
     int beta = (ell + alpha - 1) / alpha;
     size_t ln = (size_t)n;
-    u64 *ext = (u64 *)malloc(sizeof(u64) * n_ext * ln);
+    u64 ext_mods[96];
+    for (int t = 0; t < n_ext; t++) ext_mods[t] = P->mods[ext_mod_index(P, ell, t)];
+    for (int j = 0; j < beta; j++) {
+        int lo = j * alpha, hi = (j + 1) * alpha < ell ? (j + 1) * alpha : ell;
+        u64 *e = ext + (size_t)j * n_ext * ln;
+#pragma omp parallel for schedule(dynamic)
+        for (int t = 0; t < n_ext; t++) {
+            if (t >= lo && t < hi) memcpy(e + t * ln, c + t * ln, sizeof(u64) * ln);
+            else or_bconv_centred(c + lo * ln, P->mods + lo, hi - lo, e + t * ln, &ext_mods[t], 1, n);
+        }
+    }
+}
+
+/* Inner product of the ModUp digits (or_modup's layout), each limb first
+ * mapped by the automorphism X -> X^g (g = 1: unchanged), with the
+ * switching key, then ModDown to ell limbs: out0, out1. */
+void or_ks_ext(const or_params *P, const u64 *ext, int ell, const u64 *ksk, uint64_t g, u64 *out0, u64 *out1)
+{
+    int n = 1 << P->log_n, L = P->L, K = P->K, dnum = P->dnum;
+    int alpha = (L + dnum - 1) / dnum;
+    int n_ext = ell + K;
+    int beta = (ell + alpha - 1) / alpha;
+    size_t ln = (size_t)n;
     u64 *acc[2];
     acc[0] = (u64 *)calloc(n_ext * ln, sizeof(u64));
     acc[1] = (u64 *)calloc(n_ext * ln, sizeof(u64));
-    u64 *prod = (u64 *)malloc(sizeof(u64) * ln);
-    u64 ext_mods[96];
-    for (int t = 0; t < n_ext; t++) ext_mods[t] = P->mods[ext_mod_index(P, ell, t)];
-
     for (int j = 0; j < beta; j++) {
-        int lo = j * alpha, hi = (j + 1) * alpha < ell ? (j + 1) * alpha : ell;
-        /* ModUp of digit j (limbs are independent: parallel over t) */
-#pragma omp parallel for schedule(dynamic)
-        for (int t = 0; t < n_ext; t++) {
-            if (t >= lo && t < hi) {
-                memcpy(ext + t * ln, c + t * ln, sizeof(u64) * ln);
-            } else {
-                or_bconv_centred(c + lo * ln, P->mods + lo, hi - lo, ext + t * ln, &ext_mods[t], 1, n);
-            }
-        }
-        /* inner product with the key */
+        const u64 *e = ext + (size_t)j * n_ext * ln;
 #pragma omp parallel for collapse(2) schedule(dynamic)
         for (int b = 0; b < 2; b++) {
             for (int t = 0; t < n_ext; t++) {
                 int mi = ext_mod_index(P, ell, t);
                 const u64 *key = ksk + (((size_t)j * 2 + b) * (L + K) + mi) * ln;
                 u64 *pr = (u64 *)malloc(sizeof(u64) * ln);
-                or_polymul(ext + t * ln, key, pr, P->log_n, P->mods[mi], P->psis[mi]);
+                const u64 *src = e + t * ln;
+                u64 *perm = NULL;
+                if (g != 1) {
+                    perm = (u64 *)malloc(sizeof(u64) * ln);
+                    or_automorphism(src, perm, n, g, P->mods[mi]);
+                    src = perm;
+                }
+                or_polymul(src, key, pr, P->log_n, P->mods[mi], P->psis[mi]);
                 for (int k = 0; k < n; k++)
                     acc[b][t * ln + k] = addmod(acc[b][t * ln + k], pr[k], P->mods[mi]);
                 free(pr);
+                free(perm);
             }
         }
     }
@@ -412,9 +431,21 @@ void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64
                                          Pmod_inv[i], P->mods[i]);
     }
     free(conv);
-    free(prod);
     free(acc[0]);
     free(acc[1]);
+}
+
+/* Hybrid key switching of c (ell limbs, coefficient domain) with ksk
+ * ([dnum][2][L+K][n]): ModUp, inner product, ModDown. */
+void or_keyswitch(const or_params *P, const u64 *c, int ell, const u64 *ksk, u64 *out0, u64 *out1)
+{
+    int L = P->L, K = P->K, dnum = P->dnum;
+    int alpha = (L + dnum - 1) / dnum;
+    int beta = (ell + alpha - 1) / alpha;
+    size_t words = (size_t)beta * (ell + K) * ((size_t)1 << P->log_n);
+    u64 *ext = (u64 *)malloc(sizeof(u64) * words);
+    or_modup(P, c, ell, ext);
+    or_ks_ext(P, ext, ell, ksk, 1, out0, out1);
     free(ext);
 }
 

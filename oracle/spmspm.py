@@ -240,8 +240,10 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
                          counts: OpCounts | None = None) -> list:
     """Lazy accumulation of Alg. 2's products.
 
-    Alignment rotations and the tensor product are Alg. 2's.  Then, instead
-    of relinearising, rescaling, masking and rotating every product:
+    The tensor product is Alg. 2's; alignment rotations are computed per
+    source ciphertext digit by digit from the top with hoisted ModUps
+    (alignment_rotations).  Then, instead of relinearising, rescaling,
+    masking and rotating every product:
       1. each tensor product (three polynomials at the operands' level ell)
          is multiplied by its mask e_{min_slot} (at level ell, scale
          q_{ell-2}) and summed into the group of matches that share the
@@ -275,15 +277,24 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
         mask_pt = make_mask_grouped(orc, 0, ell)
     mods = orc.mods[:ell]
     mi = np.arange(ell, dtype=np.int32)
+    # every alignment rotation of a source, digit by digit from the top,
+    # each stage hoisted (alignment_rotations)
+    need = {}
+    for mt in matches:
+        ca, sa = divmod(mt.a_pos, S)
+        cb, sb = divmod(mt.b_pos, S)
+        if sa < sb:
+            need.setdefault(("B", cb), set()).add(sb - sa)
+        elif sb < sa:
+            need.setdefault(("A", ca), set()).add(sa - sb)
     rot_cache = {}
+    for (which, chunk), amts in sorted(need.items()):
+        src = (A_cts if which == "A" else B_cts)[chunk]
+        for amt, ct in alignment_rotations(orc, keys, src, sorted(amts), counts).items():
+            rot_cache[(which, chunk, amt)] = ct
 
     def rotated(which: str, chunk: int, amount: int) -> Ct:
-        key = (which, chunk, amount)
-        if key not in rot_cache:
-            src = (A_cts if which == "A" else B_cts)[chunk]
-            rot_cache[key] = orc.rotate(src, amount, keys)
-            counts.ks_align += len(rotation_plan(amount, S, P.rot_base))
-        return rot_cache[key]
+        return rot_cache[(which, chunk, amount)]
 
     groups = {}
     for mt in matches:
@@ -321,6 +332,32 @@ def spmspm_ct_ct_grouped(orc: Oracle, keys: Keys, A_csr, A_cts: list, B_csc, B_c
         done.append((key, ct))
     _rotation_tree(orc, keys, done, result, merge_digits, counts)
     return result
+
+
+def alignment_rotations(orc: Oracle, keys: Keys, src: Ct, amounts: list, counts: OpCounts) -> dict:
+    """src rotated by every amount (0 < amount < S), digit by digit from the
+    highest base-b digit down: at each digit position the ciphertexts that
+    share the higher digits are rotated by every needed digit with one hoisted
+    ModUp (Oracle.rotate_hoisted).  Returns amount -> ciphertext."""
+    P = orc.P
+    S, b = P.slots, P.rot_base
+    top = 1
+    while top * b < S:
+        top *= b
+    cur = {0: src}
+    w = top
+    while w >= 1:
+        nxt = {}
+        for H, ct in sorted(cur.items()):
+            digs = sorted({(a // w) % b for a in amounts if a - a % (w * b) == H})
+            rot = [d for d in digs if d]
+            outs = orc.rotate_hoisted(ct, [d * w for d in rot], keys) if rot else []
+            counts.ks_align += len(rot)
+            for d in digs:
+                nxt[H + d * w] = ct if d == 0 else outs[rot.index(d)]
+        cur = nxt
+        w //= b
+    return {a: cur[a] for a in amounts}
 
 
 def _rotation_tree(orc: Oracle, keys: Keys, items: list, result: list, merge_digits: bool, counts: OpCounts):

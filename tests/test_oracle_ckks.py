@@ -151,3 +151,23 @@ def test_mask_isolates_one_slot(small):
     want = np.zeros(P.slots)
     want[9] = z[9]
     assert np.max(np.abs(out - want)) < 1e-6
+
+
+def test_hoisted_rotations_decrypt_to_shifted_slots():
+    """One ModUp shared by several rotation amounts (automorphism applied to
+    the extended digits): each result decrypts to the left-shifted slots,
+    within the noise of one key switch, like the plain rotation."""
+    recipe = synthetic.ring_tiny(log_n=7, L=6, dnum=3, rot_base=4)
+    P = oracle_params(recipe)
+    o = ckks.Oracle(P)
+    keys = o.keygen(3, rot_amounts=ckks.rotation_key_amounts(P.slots, P.rot_base))
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, P.slots)
+    ct = o.encrypt(o.encode(z, P.L, P.scale), keys, rng)
+    amounts = [1, 2, 3, 4, 8, 12, 16, 48]
+    outs = o.rotate_hoisted(ct, amounts, keys)
+    for r, h in zip(amounts, outs):
+        got = np.real(o.decode(o.decrypt(h, keys)))
+        assert np.max(np.abs(got - np.roll(z, -r))) < 1e-6
+        plain = np.real(o.decode(o.decrypt(o.rotate_single(ct, r, keys), keys)))
+        assert np.max(np.abs(got - plain)) < 1e-6

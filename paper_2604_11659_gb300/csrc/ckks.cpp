@@ -41,6 +41,53 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
     moddown(ctx, items, ell, acc, acc_stride, conv, d_base, d_base_g, base_c1, out, out_stride);
 }
 
+void rotate_hoisted(Ctx &ctx, const Keys &keys, int ell, const u64 *src, const std::vector<int> &amounts, u64 *out)
+{
+    const int total = (int)amounts.size();
+    if (!total) return;
+    Runtime &rt = *ctx.rt;
+    const size_t n = ctx.n;
+    const int next = ell + ctx.K, beta = beta_of(ctx, ell);
+    const long long pstride = (long long)ell * n, cstride = 2 * pstride;
+    const long long ext_stride = (long long)beta * next * n;
+    const long long acc_stride = 2LL * next * n;
+    for (int a : amounts) rotation_key(keys, a);   // EKEY before any launch
+    struct InKs {
+        Ctx &c;
+        explicit InKs(Ctx &x) : c(x) { ++c.in_keyswitch; }
+        ~InKs() { --c.in_keyswitch; }
+    } in_ks(ctx);
+    // ModUp of the source's c1, once
+    u64 *coef = rt.workspace(WS_KS_COEF, (size_t)pstride);
+    u64 *ext = rt.workspace(WS_HOIST_EXT, (size_t)ext_stride);
+    const u64 *c1 = src + pstride;
+    copy_words(ctx, coef, c1, (size_t)pstride);
+    ntt_inverse(ctx, Batch{coef, pstride, 1, nullptr}, limb_range(0, ell, 0));
+    modup_bconv(ctx, 1, ell, coef, pstride, ext, ext_stride);
+    ntt_forward(ctx, Batch{ext, ext_stride, 1, nullptr}, modup_ntt_map(ctx, ell));
+    // per amount: inner product of the permuted extension, ModDown, c0 permuted
+    const int B = match_batch_size(ctx);
+    for (int a0 = 0; a0 < total; a0 += B) {
+        const int items = std::min(B, total - a0);
+        u64 *acc = rt.workspace(WS_KS_ACC, (size_t)items * acc_stride);
+        u64 *conv = rt.workspace(WS_KS_CONV, (size_t)items * 2 * ell * n);
+        std::vector<const u64 *> own(items, c1), base(items, src);
+        std::vector<int> srci(items, 0), g(items);
+        std::vector<KeyGroup> groups;
+        for (int i = 0; i < items; ++i) {
+            g[i] = galois_element(ctx, amounts[a0 + i]);
+            groups.push_back(KeyGroup{rotation_key(keys, amounts[a0 + i]), i, 1});
+        }
+        ctx.prof.ks_calls += items;
+        ctx.prof.ks_bytes += 8.0 * n * (3.0 * ell * items + 2.0 * beta * next * items);
+        const int *d_g = rt.upload_vec(g);
+        ks_inner_product(ctx, items, ell, rt.upload_vec(own), ext, ext_stride, groups, acc, acc_stride,
+                         rt.upload_vec(srci), d_g);
+        moddown(ctx, items, ell, acc, acc_stride, conv, rt.upload_vec(base), d_g, false, out + (long long)a0 * cstride,
+                cstride);
+    }
+}
+
 int galois_element(const Ctx &ctx, int r)
 {
     const long long two_n = 2LL * ctx.n;

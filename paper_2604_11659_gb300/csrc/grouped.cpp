@@ -22,6 +22,12 @@
 // chunks.  Relinearisation and rotation are linear, so the products decrypt
 // like Alg. 2's, with fewer key switches; the ciphertext bits differ.
 //
+// Alignment rotations (ct x ct) are computed per source ciphertext digit by
+// digit from the highest base-b digit down: at each digit position, the
+// ciphertexts that share the higher digits are rotated by every needed digit
+// with one hoisted ModUp (rotate_hoisted), so a source needs one key switch
+// per distinct (higher digits, nonzero digit) and one ModUp per stage input.
+//
 // Groups arrive at the tree in ascending (chunk, r) order, so a sum of the
 // tree is complete as soon as the stream has passed its range of amounts and
 // no sum at a lower level within that range is still pending; sums are
@@ -34,6 +40,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <set>
 
 #include "engine.h"
 
@@ -334,11 +341,30 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
         const long long t = (long long)mt.i * B.cols + mt.j;
         groups[{(int)(t / S), ((g.slot - t % S) % S + S) % S}].push_back((int)x);
     }
-    // every key the call will use, before anything is launched
-    for (auto &a : aligns)
-        for (int s : rotation_plan(ctx, std::get<2>(a))) rotation_key(keys, s);
+    // alignment plan: per source ciphertext, its amounts digit by digit from
+    // the top; one hoisted rotation batch per (source, higher digits)
+    const long long b = ctx.rot_base;
+    long long top = 1;
+    while (top * b < S) top *= b;
+    std::map<std::pair<int, int>, std::vector<int>> by_src;   // (operand, chunk) -> alignment ids
+    for (size_t a = 0; a < aligns.size(); ++a)
+        by_src[{std::get<0>(aligns[a]), std::get<1>(aligns[a])}].push_back((int)a);
+    size_t n_rot = 0;
+    for (auto &kv : by_src)
+        for (long long w = top; w >= 1; w /= b) {
+            std::set<std::pair<long long, int>> st;
+            for (int a : kv.second) {
+                const long long amt = std::get<2>(aligns[a]);
+                const int d = (int)((amt / w) % b);
+                if (d) {
+                    st.insert({amt - amt % (w * b), d});
+                    rotation_key(keys, (int)(d * w));   // every key, before anything is launched
+                }
+            }
+            n_rot += st.size();
+        }
     for (auto &kv : groups) DigitTree::check_keys(ctx, keys, kv.first.second, merge);
-    need_memory(aligns.size() * (size_t)csL * sizeof(u64), "the alignment store");
+    need_memory(n_rot * (size_t)csL * sizeof(u64), "the alignment rotations");
 
     uint64_t st_align = 0, st_relin = 0, st_rescales = 0, st_final = 0;
     std::vector<Ct *> res(nC, nullptr);
@@ -362,23 +388,38 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             for (int i = 0; i < ell; ++i) mi[i] = i;
             to_montgomery(ctx, mask, ell, mi.data(), 1);
 
-            // ---- alignment store ----
+            // ---- alignment rotations: per source, digit by digit from the
+            // top, the ciphertexts sharing the higher digits rotated by every
+            // needed digit with one hoisted ModUp ----
             const int Bm = match_batch_size(ctx);
-            u64 *store = aligns.empty() ? nullptr : sc.words(aligns.size() * (size_t)csL);
-            for (size_t a0 = 0; a0 < aligns.size(); a0 += Bm) {
-                const size_t a1 = std::min(aligns.size(), a0 + Bm);
-                std::vector<const u64 *> in;
-                std::vector<int> amt;
-                for (size_t a = a0; a < a1; ++a) {
-                    const int op = std::get<0>(aligns[a]), chunk = std::get<1>(aligns[a]);
-                    in.push_back((op == 0 ? Ach[chunk] : Bch[chunk])->d);
-                    amt.push_back(std::get<2>(aligns[a]));
+            std::vector<const u64 *> aligned(aligns.size(), nullptr);
+            for (auto &kv : by_src) {
+                const u64 *src = (kv.first.first == 0 ? Ach[kv.first.second] : Bch[kv.first.second])->d;
+                std::map<long long, const u64 *> cur{{0, src}};
+                for (long long w = top; w >= 1; w /= b) {
+                    std::map<long long, const u64 *> nxt;
+                    for (auto &ck : cur) {
+                        std::set<int> digs;
+                        for (int a : kv.second) {
+                            const long long amt = std::get<2>(aligns[a]);
+                            if (amt - amt % (w * b) == ck.first) digs.insert((int)((amt / w) % b));
+                        }
+                        std::vector<int> amts;
+                        for (int d : digs)
+                            if (d) amts.push_back((int)(d * w));
+                        u64 *o = amts.empty() ? nullptr : sc.words(amts.size() * (size_t)csL);
+                        rotate_hoisted(ctx, keys, ell, ck.second, amts, o);
+                        st_align += amts.size();
+                        size_t r = 0;
+                        for (int d : digs) nxt[ck.first + d * w] = d ? o + (long long)(r++) * csL : ck.second;
+                    }
+                    cur.swap(nxt);
                 }
-                rotate_batch(ctx, keys, ell, in, amt, store + (long long)a0 * csL, &st_align);
+                for (int a : kv.second) aligned[a] = cur.at(std::get<2>(aligns[a]));
             }
             auto operand = [&](int src, bool a_side) -> const u64 * {
                 if (src < 0) return (a_side ? Ach[-src - 1] : Bch[-src - 1])->d;
-                return store + (long long)src * csL;
+                return aligned[src];
             };
 
             DigitTree tree(ctx, keys, ell - 2, merge, res);

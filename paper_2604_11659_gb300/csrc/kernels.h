@@ -67,8 +67,12 @@ struct KeyGroup {
     const u64 *key;    // [dnum][2][M][n] Montgomery form
     int first, count;  // items [first, first + count)
 };
+// Hoisted form (src_of, perm_g device arrays, else nullptr): item it reads
+// the extension of source src_of[it] and in[it] through the automorphism
+// X -> X^perm_g[it].
 void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const u64 *ext, long long ext_stride,
-                      const std::vector<KeyGroup> &groups, u64 *acc, long long acc_stride);
+                      const std::vector<KeyGroup> &groups, u64 *acc, long long acc_stride,
+                      const int *src_of = nullptr, const int *perm_g = nullptr);
 
 // ModDown: acc [items][2][ell+K][n] NTT domain.  P-limbs are inverse
 // transformed in place, converted into conv [items][2][ell][n] (coefficient),

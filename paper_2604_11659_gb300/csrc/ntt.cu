@@ -489,10 +489,9 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
     for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
     __syncthreads();
     if constexpr (MODE == kFuseNone) {
-        // st.global: the next shared-memory load need not wait for the store
         for (int x = threadIdx.x; x < kElems; x += 256) {
             const u64 y = sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))];
-            __stcg(p + e0 + x, reduce_any(y, q, m.one_p));
+            p[e0 + x] = reduce_any(y, q, m.one_p);
         }
     } else if constexpr (MODE == kFuseModDown) {
         // out_b[i] = base_b[sigma(k)] + (acc_b[i] - conv_b[i]) P^{-1} (conv = this transform)

@@ -204,6 +204,46 @@ __global__ void __launch_bounds__(256) k_ip(int ell, int L, int K, int alpha, in
     }
 }
 
+// Hoisted inner product: item it reads the extension of source src_of[it]
+// and its own limbs in[it] through the automorphism X -> X^perm_g[it]
+// (evaluation rep.: slot k reads slot perm_index(k, g)); one key per group.
+__global__ void __launch_bounds__(256) k_ip_hoisted(int ell, int L, int K, int alpha, int M, int log_n,
+                                                    const u64 *const *in, const u64 *__restrict__ ext,
+                                                    long long ext_stride, IpGroups groups, u64 *__restrict__ acc,
+                                                    long long acc_stride, const ModConst *__restrict__ mc,
+                                                    const int *__restrict__ src_of, const int *__restrict__ perm_g)
+{
+    const int n = 1 << log_n;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int t = blockIdx.y;
+    const IpGroup gr = groups.g[blockIdx.z];
+    const int next = ell + K;
+    const int gm = t < ell ? t : L + (t - ell);
+    const ModConst m = mc[gm];
+    const int own = t < ell ? t / alpha : -1;
+    const int beta = (ell + alpha - 1) / alpha;
+    for (int it = gr.first; it < gr.first + gr.count; ++it) {
+        const int ks = perm_index(k, (unsigned)perm_g[it], log_n);
+        const u64 *e_it = ext + src_of[it] * ext_stride + (size_t)t * n + ks;
+        Acc30 a0, a1;
+        acc30_zero(a0);
+        acc30_zero(a1);
+        for (int j = 0; j < beta; ++j) {
+            const u64 e = (j == own) ? in[it][(size_t)t * n + ks] : e_it[(size_t)j * next * n];
+            uint32_t e0, e1, q0, q1;
+            split30(e, e0, e1);
+            split30(__ldg(gr.key + (((size_t)j * 2 + 0) * M + gm) * n + k), q0, q1);
+            acc30_mac(a0, e0, e1, (u64)q0 | ((u64)q1 << 32));
+            split30(__ldg(gr.key + (((size_t)j * 2 + 1) * M + gm) * n + k), q0, q1);
+            acc30_mac(a1, e0, e1, (u64)q0 | ((u64)q1 << 32));
+        }
+        u64 *o = acc + it * acc_stride;
+        o[(size_t)t * n + k] = redc(acc30_value(a0), m.q, m.qneg_inv);
+        o[((size_t)next + t) * n + k] = redc(acc30_value(a1), m.q, m.qneg_inv);
+    }
+}
+
 // ModDown basis conversion P -> Q_ell of the CENTRED representative of the
 // accumulator modulo P: with y_k = [acc_k (P/p_k)^{-1}]_{p_k},
 //   sum_k y_k (P/p_k) = (acc mod P) + u P,  u = floor(sum_k y_k / p_k),
@@ -659,7 +699,8 @@ LimbMap modup_ntt_map(const Ctx &ctx, int ell)
 }
 
 void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const u64 *ext, long long ext_stride,
-                      const std::vector<KeyGroup> &groups, u64 *acc, long long acc_stride)
+                      const std::vector<KeyGroup> &groups, u64 *acc, long long acc_stride, const int *src_of,
+                      const int *perm_g)
 {
     for (size_t g0 = 0; g0 < groups.size(); g0 += kMaxIpGroups) {
         const int cnt = (int)std::min<size_t>(kMaxIpGroups, groups.size() - g0);
@@ -675,7 +716,10 @@ void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const 
             const dim3 grid = grid_n(ctx.n, ell + ctx.K, cnt);
 #define SPFHE_IP(BB) k_ip<BB><<<grid, kT, 0, ctx.stream>>>(ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, in, ext, \
                                                            ext_stride, hg, acc, acc_stride, ctx.dt.mc)
-            switch ((int)beta_ip) {
+            if (src_of)
+                k_ip_hoisted<<<grid, kT, 0, ctx.stream>>>(ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.log_n, in, ext,
+                                                          ext_stride, hg, acc, acc_stride, ctx.dt.mc, src_of, perm_g);
+            else switch ((int)beta_ip) {
             case 1: SPFHE_IP(1); break;
             case 2: SPFHE_IP(2); break;
             case 3: SPFHE_IP(3); break;

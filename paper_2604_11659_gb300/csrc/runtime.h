@@ -49,6 +49,7 @@ enum WsSlot {
     WS_MISC,
     WS_GRP_SUM,
     WS_TREE_ROT,
+    WS_HOIST_EXT,
 };
 
 // ---- batched evaluator (ckks.cpp) ----
@@ -70,7 +71,14 @@ void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u
 void rotate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell, const std::vector<const u64 *> &in,
                   const std::vector<int> &r, u64 *out, uint64_t *ks);
 
+// Rotations of one ciphertext src ([2][ell][n]) by every amount (each with a
+// key of its own, 0 < amount < S) sharing one ModUp of its c1: the
+// automorphism is applied to the extended digits in the inner product.
+// out [amounts][2][ell][n].
+void rotate_hoisted(Ctx &ctx, const Keys &keys, int ell, const u64 *src, const std::vector<int> &amounts, u64 *out);
+
 std::vector<int> rotation_plan(const Ctx &ctx, long long r);
+int match_batch_size(const Ctx &ctx);   // matches per batch (engine.cpp)
 int galois_element(const Ctx &ctx, int r);   // 5^r mod 2n
 const u64 *rotation_key(const Keys &keys, int amount);
 

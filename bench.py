@@ -296,20 +296,38 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
         outs, st = sp.spfhe_sparse_matmul_batch(ctx, reqs, ncs)
         return outs, sum(x["matches"] for x in st)
 
+    # the batched call captured once as one CUDA graph, then launched
+    t0 = time.perf_counter()
+    graph = sp.spfhe_matmul_graph_create_batch(ctx, reqs, 0)
+    capture_s = time.perf_counter() - t0
+
+    def graphed():
+        sp.spfhe_matmul_graph_launch(graph)
+        return [], None
+
     res = {}
-    for name, fn in (("plain", per_product(1)), ("per_product", per_product(0)), ("batched", batched)):
-        outs, m = fn()   # warm-up
+    for name, fn in (("plain", per_product(1)), ("per_product", per_product(0)), ("batched", batched),
+                     ("graph", graphed)):
+        outs, _ = fn()   # warm-up
         for o in outs:
             for h in o:
                 sp.spfhe_ct_free(h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        outs, m = fn()
+        outs, mm = fn()
         torch.cuda.synchronize()
         res[name] = time.perf_counter() - t0
+        if mm is not None:
+            m = mm
         for o in outs:
             for h in o:
                 sp.spfhe_ct_free(h)
+    sp.spfhe_sync(ctx)
+    g_outs, g_st = sp.spfhe_matmul_graph_results_batch(graph, ncs)
+    for o in g_outs:
+        for h in o:
+            sp.spfhe_ct_free(h)   # handles only: the chunks belong to the graph
+    sp.spfhe_matmul_graph_free(graph)
     for Am, a, Bm, b, nc in prods:
         for h in a + b:
             sp.spfhe_ct_free(h)
@@ -322,7 +340,10 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
             "batched_s": res["batched"],
             "products_per_s_plain": count / res["plain"], "products_per_s_batched": count / res["batched"],
             "speedup": res["plain"] / res["batched"],
-            "speedup_over_per_product_batching": res["per_product"] / res["batched"]}
+            "speedup_over_per_product_batching": res["per_product"] / res["batched"],
+            "graph_s": res["graph"], "graph_capture_s": round(capture_s, 2),
+            "graph_kernels": int(g_st[0]["launches"]),
+            "products_per_s_graph": count / res["graph"]}
 
 
 def dense_layer_pt(stream, rot_base=16):

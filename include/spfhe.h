@@ -448,12 +448,23 @@ spfhe_status spfhe_server_destroy(spfhe_server *srv);
 typedef struct spfhe_graph spfhe_graph;
 spfhe_status spfhe_matmul_graph_create(spfhe_ctx *ctx, const spfhe_matmul_req *req, int variant,
                                        spfhe_graph **out);
+/* n_req >= 1 products captured into one graph.  variant 0: planned together
+ * as spfhe_sparse_matmul_batch does (requests at the same level share
+ * launches); variant 1: the grouped products one after another.  Each
+ * request's results are bit-identical to its single call's.  Buffers the
+ * products free while they are captured stay with the graph until
+ * spfhe_matmul_graph_free, so the graph holds the sum of the products'
+ * working sets (ENOMEM when they do not fit).  spfhe_matmul_graph_create is
+ * this call with one request. */
+spfhe_status spfhe_matmul_graph_create_batch(spfhe_ctx *ctx, size_t n_req, const spfhe_matmul_req *reqs,
+                                             int variant, spfhe_graph **out);
 /* Enqueue one launch of the graph on the context stream (asynchronous):
  * zeroes the result chunks and recomputes the product into them. */
 spfhe_status spfhe_matmul_graph_launch(spfhe_graph *g);
-/* Handles of the graph's n_c result chunks (valid after a launch completes)
- * and the product's counters; spfhe_ct_free on these handles frees only the
- * handle, the chunks belong to the graph. */
+/* Handles of the graph's n_c result chunks (valid after a launch completes;
+ * n_c = the sum over its requests, request after request) and the products'
+ * counters (stats: NULL or one entry per request); spfhe_ct_free on these
+ * handles frees only the handle, the chunks belong to the graph. */
 spfhe_status spfhe_matmul_graph_results(spfhe_graph *g, spfhe_ct **C_chunks, size_t n_c, spfhe_stats *stats);
 /* Wait for the context stream and free the graph and everything it owns. */
 void spfhe_matmul_graph_free(spfhe_graph *g);

@@ -107,5 +107,9 @@ void spmspm_ct_pt_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
                           const spfhe_sparse_meta &B, const double *Bvals, Pt *const *Bpts, bool merge_digits,
                           Ct **C, size_t nC, spfhe_stats *out_stats);
 size_t result_chunks(const Ctx &ctx, const spfhe_matmul_req &r);
+// many ct x ct products through one task engine (serve.cpp); C receives
+// every request's chunks, request after request
+void sparse_matmul_batch(Ctx &ctx, size_t n_req, const spfhe_matmul_req *reqs, Ct **C, size_t n_c_total,
+                         spfhe_stats *stats);
 
 }  // namespace spfhe

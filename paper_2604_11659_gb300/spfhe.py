@@ -133,6 +133,8 @@ _SIGS += [
                                                  ctypes.POINTER(handle)]),
     ("spfhe_matmul_graph_results", ctypes.c_int, [handle, ctypes.POINTER(handle), ctypes.c_size_t,
                                                   ctypes.POINTER(Stats)]),
+    ("spfhe_matmul_graph_create_batch", ctypes.c_int, [handle, ctypes.c_size_t, ctypes.POINTER(MatmulReq),
+                                                       ctypes.c_int, ctypes.POINTER(handle)]),
     ("spfhe_sparse_matmul_batch", ctypes.c_int, [handle, ctypes.c_size_t, ctypes.POINTER(MatmulReq),
                                                  ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
     ("spfhe_server_create", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
@@ -556,6 +558,26 @@ def spfhe_matmul_graph_create(ctx, req, variant: int = 0):
     out = handle()
     _check(lib().spfhe_matmul_graph_create(ctx, ctypes.byref(req), int(variant), ctypes.byref(out)))
     return out
+
+
+def spfhe_matmul_graph_create_batch(ctx, reqs, variant: int = 0):
+    arr = (MatmulReq * max(1, len(reqs)))(*reqs)
+    out = handle()
+    _check(lib().spfhe_matmul_graph_create_batch(ctx, len(reqs), arr, int(variant), ctypes.byref(out)))
+    return out
+
+
+def spfhe_matmul_graph_results_batch(g, n_c_per_req):
+    """Every request's result handles (a list per request) and counters."""
+    total = sum(n_c_per_req)
+    outs = (handle * max(1, total))()
+    st = (Stats * max(1, len(n_c_per_req)))()
+    _check(lib().spfhe_matmul_graph_results(g, outs, total, st))
+    res, o = [], 0
+    for k in n_c_per_req:
+        res.append([handle(outs[o + i]) for i in range(k)])
+        o += k
+    return res, [st[i].as_dict() for i in range(len(n_c_per_req))]
 
 
 def spfhe_matmul_graph_launch(g):

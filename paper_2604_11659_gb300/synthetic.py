@@ -189,6 +189,43 @@ def tiny_case(seed: int, d: int, sparsity: float, log_n: int = 6, L: int = 4, dn
                       ring_tiny(log_n, L, dnum, rot_base))
 
 
+def edge_cases(seed: int = 40, log_n: int = 6, rot_base: int = 4) -> dict:
+    """Degenerate and boundary shapes on a tiny ring (S = 2^(log_n-1) slots):
+    a 1x1x1 product, a dot product (1 x 9 x 1), an outer product (inner
+    dimension 1), a result of exactly S slots, one of S + 1 (a one-slot
+    second chunk), an all-zero row of A with an all-zero column of B, a single
+    match far from slot 0, and an operand of S + 1 nonzeros (a one-slot
+    second operand chunk)."""
+    rng = np.random.default_rng(seed)
+    ring = ring_tiny(log_n, 4, 1, rot_base)
+    S = 1 << (log_n - 1)
+    out = {}
+
+    def add(name, A, B):
+        out[name] = MatmulCase(name, rescale_rows_to_unit_output(A, B), B, ring)
+
+    add("scalar_1x1x1", np.array([[0.7]]), np.array([[-0.9]]))
+    add("dot_1x9x1", rng.uniform(-1, 1, (1, 9)), rng.uniform(-1, 1, (9, 1)))
+    add("outer_6x1x5", rng.uniform(-1, 1, (6, 1)), rng.uniform(-1, 1, (1, 5)))
+    add("result_S", bernoulli_sparse(rng, 4, 3, 0.3), bernoulli_sparse(rng, 3, S // 4, 0.3))
+    add("result_S_plus_1", bernoulli_sparse(rng, 3, 4, 0.3), bernoulli_sparse(rng, 4, (S + 3) // 3, 0.3))
+    A = bernoulli_sparse(rng, 5, 5, 0.3)
+    B = bernoulli_sparse(rng, 5, 5, 0.3)
+    A[2] = 0.0
+    B[:, 3] = 0.0
+    add("zero_row_and_col_5x5", A, B)
+    A = np.zeros((8, 8))
+    B = np.zeros((8, 8))
+    A[7, 5] = 0.8
+    B[5, 6] = -0.6
+    add("single_match_8x8", A, B)
+    d = 6
+    A = rng.uniform(-1, 1, (d, d))
+    A.flat[rng.choice(d * d, d * d - (S + 1), replace=False)] = 0.0
+    add("operand_S_plus_1_nnz", A, bernoulli_sparse(rng, d, d, 0.5))
+    return out
+
+
 @dataclass
 class ServeRequest:
     case: MatmulCase

@@ -118,3 +118,70 @@ def _ntt_key(p, k):
         for b in range(2):
             out[j, b] = p.o.rns_ntt(k[j, b], mi)
     return out
+
+
+def test_graph_batch_equals_alone(setup):
+    """Every request of the batch captured into one CUDA graph (one task
+    engine over all of them, mixed levels): two launches, each request's
+    chunks equal to its single call's, counters equal."""
+    p = setup
+    sp = p.spfhe
+    g = sp.spfhe_matmul_graph_create_batch(p.ctx, [_req(p, r) for r in p.reqs], 0)
+    try:
+        for _ in range(2):
+            sp.spfhe_matmul_graph_launch(g)
+            sp.spfhe_sync(p.ctx)
+            outs, stats = sp.spfhe_matmul_graph_results_batch(g, [r.n_c for r in p.reqs])
+            for r, hs, st in zip(p.reqs, outs, stats):
+                for h, a in zip(hs, r.alone):
+                    assert np.array_equal(p.export_ct(h), a)
+                    sp.spfhe_ct_free(h)   # the handle only
+                for k in ("matches", "ks_relin", "ks_align", "ks_final", "rescales"):
+                    assert st[k] == r.stats[k]
+    finally:
+        sp.spfhe_matmul_graph_free(g)
+
+
+def test_graph_batch_grouped_equals_alone(setup):
+    """The grouped variant over the same requests in one graph (products one
+    after another, the library's own masks): each equal to its single grouped
+    call."""
+    p = setup
+    sp = p.spfhe
+    alone = []
+    for r in p.reqs:
+        hs, st = sp.spfhe_sparse_matmul_ct_ct_grouped(p.ctx, p.gkeys, r.Am, r.gA, r.Bm, r.gB, None, r.n_c)
+        alone.append(([p.export_ct(p.track("ct", h)) for h in hs], st))
+    reqs = [sp.matmul_req(p.gkeys, r.Am, r.gA, r.Bm, r.gB, None) for r in p.reqs]
+    g = sp.spfhe_matmul_graph_create_batch(p.ctx, reqs, 1)
+    try:
+        sp.spfhe_matmul_graph_launch(g)
+        sp.spfhe_sync(p.ctx)
+        outs, stats = sp.spfhe_matmul_graph_results_batch(g, [r.n_c for r in p.reqs])
+        for (want, st0), hs, st in zip(alone, outs, stats):
+            for h, a in zip(hs, want):
+                assert np.array_equal(p.export_ct(h), a)
+                sp.spfhe_ct_free(h)
+            for k in ("matches", "ks_relin", "ks_align", "ks_final", "rescales"):
+                assert st[k] == st0[k]
+    finally:
+        sp.spfhe_matmul_graph_free(g)
+
+
+def test_graph_batch_errors(setup):
+    """A request without rotation keys fails the capture with EKEY and leaves
+    the context usable; an empty request list is EINVAL."""
+    p = setup
+    sp = p.spfhe
+    relin_only = p.track("keys", sp.spfhe_keys_import(p.ctx, p.keys.s, _ntt_key(p, p.keys.relin), {}))
+    reqs = [_req(p, p.reqs[0]), _req(p, p.reqs[2], keys=relin_only)]
+    with pytest.raises(sp.SpfheError) as e:
+        sp.spfhe_matmul_graph_create_batch(p.ctx, reqs, 0)
+    assert e.value.status == -4
+    with pytest.raises(sp.SpfheError) as e:
+        sp.spfhe_matmul_graph_create_batch(p.ctx, [], 0)
+    assert e.value.status == -1
+    r = p.reqs[1]
+    hs, _ = sp.spfhe_sparse_matmul_ct_ct(p.ctx, p.gkeys, r.Am, r.gA, r.Bm, r.gB, r.gmask, r.n_c)
+    for h, a in zip(hs, r.alone):
+        assert np.array_equal(p.export_ct(p.track("ct", h)), a)

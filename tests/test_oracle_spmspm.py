@@ -290,3 +290,24 @@ def test_ct_pt_grouped_matches_fp64_and_counts(seed, rows, inner, cols, s, rot_b
     _, _, _, _, C_n, nom, _ = _run(case, rot_base=rot_base, variant="ptgrouped_nomerge")
     assert np.max(np.abs(C_n - spmspm.matmul_fp64(case.A, case.B))) < 1e-4
     assert nom.ks_final >= counts.ks_final
+
+
+# ---- degenerate and boundary shapes -------------------------------------------
+EDGE = synthetic.edge_cases()
+
+
+def _dense_match_count(A, B):
+    """Alg. 1's matches counted from the dense matrices: for every inner index
+    k, each nonzero of column k of A meets each nonzero of row k of B."""
+    return int(sum(np.count_nonzero(A[:, k]) * np.count_nonzero(B[k, :]) for k in range(A.shape[1])))
+
+
+@pytest.mark.parametrize("variant", ["ct_ct", "grouped", "ct_pt", "ptgrouped"])
+@pytest.mark.parametrize("name", list(EDGE))
+def test_edge_shapes_match_fp64(name, variant):
+    case = EDGE[name]
+    o, P, keys, res, C, counts, _ = _run(case, rot_base=case.ring.rot_base, variant=variant)
+    rows, cols = case.A.shape[0], case.B.shape[1]
+    assert len(res) == max(1, -(-(rows * cols) // P.slots))
+    assert counts.matches == _dense_match_count(case.A, case.B)
+    assert np.max(np.abs(C - spmspm.matmul_fp64(case.A, case.B))) < 1e-4

@@ -310,7 +310,7 @@ void Engine::run_matches(int ell, const std::vector<int> &ids, const u64 *align,
     std::vector<KeyGroup> groups;
     for (int i = 0; i < m; ++i) {
         const u64 *key = kk[i]->relin;
-        if (!groups.empty() && groups.back().key == key && groups.back().count < 4)
+        if (!groups.empty() && groups.back().key == key && groups.back().count < kRelinShare)
             ++groups.back().count;
         else
             groups.push_back(KeyGroup{key, i, 1});

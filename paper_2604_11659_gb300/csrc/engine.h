@@ -89,6 +89,9 @@ class Engine {
 };
 
 int match_batch_size(const Ctx &ctx);
+// matches of one batch that share a relinearisation key read in the inner
+// product (one CTA loads the key values once and serves them all)
+constexpr int kRelinShare = 8;
 // fill a job from a single-product call (metadata is copied)
 void fill_job(Job &job, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
               const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, size_t nC);

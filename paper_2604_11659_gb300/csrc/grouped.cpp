@@ -487,7 +487,8 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
                 }
                 rescale(ctx, k, ell, rt.upload_vec(g0), T, R1, t31, 3);
                 std::vector<KeyGroup> kg;
-                for (int g = 0; g < k; g += 4) kg.push_back(KeyGroup{keys.relin, g, std::min(4, k - g)});
+                for (int g = 0; g < k; g += kRelinShare)
+                    kg.push_back(KeyGroup{keys.relin, g, std::min(kRelinShare, k - g)});
                 keyswitch_batch(ctx, k, ell - 1, rt.upload_vec(d2), kg, rt.upload_vec(base), nullptr, true, R2, cs1);
                 st_relin += k;
                 rescale(ctx, k, ell - 1, rt.upload_vec(x1), T, X, cs2, 2);

@@ -30,13 +30,29 @@ sys.path.insert(0, ROOT)
 METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); keyswitch HBM GB/s; p99"
 ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", "moddown_bconv"}
 
-# DRAM bytes (read + write) per limb of one pass, from ncu captures of the
-# radix-16 kernels on the profiler case (bench.py --small-case: n = 2^16,
-# 288 limbs per launch, one launch each of pass A and pass B); the transform
-# classes' traffic per launch is this times the launch's limbs (assumes the
-# traffic grows in proportion to the limbs).
-NTT_DRAM_BYTES_PER_LIMB = {"ks_ntt_fwd": (239.771e6 / 288 + 287.337e6 / 288) / 2,
-                           "ntt_fwd": (239.771e6 / 288 + 287.337e6 / 288) / 2}
+# DRAM bytes (read + write) per limb of each forward-transform pass kind, from
+# ncu captures of the radix-16 kernels (4 CTAs per SM, split 8/8) on the
+# profiler case (bench.py --small-case --ntt-variant 3: n = 2^16, 288-345 limbs
+# per launch): pass A, pass B, and pass B with the fused ModDown epilogue.
+NTT_FWD_DRAM_PER_LIMB = {"a": (151.2e6 + 90.8e6) / 288, "b": (250.2e6 + 138.6e6) / 345,
+                         "b_moddown": (456.6e6 + 150.7e6) / 288}
+
+
+def ks_ntt_fwd_traffic(work, nbytes, launches, n, log_n):
+    """DRAM bytes per launch of the key-switching forward transforms.  The
+    class's limbs are split by pass kind from its totals: every limb costs
+    (n/2)·log2(n) butterflies over its two passes, and every pass-B launch
+    pairs with a pass-A launch, so pass-A limbs LA = work / ((n/2)·log2 n);
+    algorithmic bytes are 16n per limb of pass A or plain pass B and 40n per
+    limb of the fused ModDown pass B, so fused limbs LF = (bytes - 32n·LA) /
+    24n and plain pass-B limbs LB = LA - LF.  Assumes DRAM bytes grow in
+    proportion to the limbs (the profiler case and the bench both stream
+    limbs far larger than L2 with the same per-limb access pattern)."""
+    la = work / (0.5 * n * log_n)
+    lf = min(la, max(0.0, (nbytes - 32.0 * n * la) / (24.0 * n)))
+    lb = la - lf
+    d = NTT_FWD_DRAM_PER_LIMB
+    return (la * d["a"] + lb * d["b"] + lf * d["b_moddown"]) / max(1, launches)
 
 
 def load_peaks():
@@ -800,8 +816,8 @@ def main():
         achieved = dd["work"] / (dd["ms"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tmulmod/s", "frac": achieved / peak,
-                "traffic": (NTT_DRAM_BYTES_PER_LIMB[dom] * dd["bytes"] / max(1, dd["launches"]) / (16.0 * g.n)
-                            if dom in NTT_DRAM_BYTES_PER_LIMB else None),
+                "traffic": (ks_ntt_fwd_traffic(dd["work"], dd["bytes"], dd["launches"], g.n, g.rec.log_n)
+                            if dom == "ks_ntt_fwd" else None),
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
                 "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
                 "work_per_launch": dd["work"] / max(1, dd["launches"]),

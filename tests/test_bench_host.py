@@ -1,0 +1,24 @@
+"""Host-side arithmetic of bench.py (no GPU): the DRAM-traffic estimate of
+the key-switching forward transforms recovers the pass mix it is built from."""
+import bench
+
+
+def test_ks_ntt_fwd_traffic_recovers_pass_mix():
+    n, log_n = 1 << 16, 16
+    la, lb, lf = 120.0, 70.0, 50.0          # pass-A, plain pass-B, fused pass-B limbs
+    work = 0.5 * n * 8 * la + 0.5 * n * 8 * (lb + lf)
+    nbytes = 16.0 * n * (la + lb) + 40.0 * n * lf
+    launches = 6
+    d = bench.NTT_FWD_DRAM_PER_LIMB
+    want = (la * d["a"] + lb * d["b"] + lf * d["b_moddown"]) / launches
+    got = bench.ks_ntt_fwd_traffic(work, nbytes, launches, n, log_n)
+    assert abs(got - want) < 1e-6 * want
+
+
+def test_ks_ntt_fwd_traffic_without_fused_passes():
+    n, log_n = 1 << 16, 16
+    la = 64.0
+    work = 0.5 * n * log_n * la
+    got = bench.ks_ntt_fwd_traffic(work, 32.0 * n * la, 2, n, log_n)
+    d = bench.NTT_FWD_DRAM_PER_LIMB
+    assert abs(got - la * (d["a"] + d["b"]) / 2) < 1e-6 * got

@@ -72,6 +72,28 @@ def alu_peak_mulmods(sm_mhz: float) -> float:
     return 152 * 64 * sm_mhz * 1e6 / 10.0
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of the product a rank multiplies: every rank runs its own,
+    independent product (weak scaling, no data-path collective)."""
+    return seed + rank
+
+
+def max_over_ranks(dist, x: float, device: str) -> float:
+    """Largest x over all ranks (x itself on one rank): the job's time is the
+    slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     def __init__(self, index: int):
         self.index = index
@@ -669,7 +691,8 @@ def main():
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
+    dev = "cuda"
 
     def barrier():
         if dist is not None:
@@ -678,7 +701,7 @@ def main():
     from paper_2604_11659_gb300 import build as gbuild
     gbuild.build()
     stream = torch.cuda.current_stream().cuda_stream
-    case = make_workload(args.workload, args.seed + rank)
+    case = make_workload(args.workload, rank_seed(args.seed, rank))
     g = GpuMatmul(case, args.rot_base, stream, ntt_chunk=args.ntt_chunk)
     sp = g.sp
 
@@ -716,12 +739,9 @@ def main():
     sp.spfhe_prof_enable(g.ctx, False)
     err = g.check(last)
     g.free(last)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(dist, ms_total, dev)
     ms_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(world, args.steps, ms_total / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     Lr = g.rec.L
@@ -742,11 +762,8 @@ def main():
         g.free(outs + ga + gb)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world / e2e_s
+    e2e_s = max_over_ranks(dist, e2e_s, dev)
+    e2e_val = whole_job_rate(world, 1, e2e_s)
 
     # the same product captured once as a CUDA graph, then launched as one unit
     graph = None
@@ -789,15 +806,12 @@ def main():
         ev1.record()
         torch.cuda.synchronize()
         ms_g = ev0.elapsed_time(ev1) / args.grouped_steps
-        if dist is not None:
-            t = torch.tensor([ms_g], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_g = float(t.item())
+        ms_g = max_over_ranks(dist, ms_g, dev)
         err_g = g.check(outs)
         g.free(outs)
         variant = {"name": "lazy accumulation (group by result chunk and final rotation amount, digit-by-digit "
                            "rotation merge); not Alg. 2's op order, parity against the oracle's grouped variant",
-                   "value": world * 1e3 / ms_g, "unit": "matmuls/s", "ms_per_step": ms_g, "steps": args.grouped_steps,
+                   "value": whole_job_rate(world, 1, ms_g / 1e3), "unit": "matmuls/s", "ms_per_step": ms_g, "steps": args.grouped_steps,
                    "warmup": 1, "max_abs_err": err_g, "ks_per_step": st_g["ks_relin"] + st_g["ks_align"] + st_g["ks_final"],
                    "ks_relin": st_g["ks_relin"], "ks_align": st_g["ks_align"], "ks_final": st_g["ks_final"],
                    "speedup_vs_alg2": ms_step / ms_g}

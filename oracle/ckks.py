@@ -21,7 +21,7 @@ COEFFICIENT domain.  Random draws (secret, masks a, errors e) come from a
 numpy Generator seeded by the caller; they are inputs, and are exported with
 the keys so that another implementation can be fed the same values.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   R1 special primes K raised to ceil(bits(largest digit)/60) (hybrid key
      switching needs P >= the digit modulus; dnum kept as configured);
   R2 primes q = 1 mod 2n searched downward from 2^b; psi the first

@@ -82,3 +82,88 @@ def test_bench_workload_decrypts_within_tolerance():
         for h in g.A_cts + g.B_cts:
             g.sp.spfhe_ct_free(h)
         g.sp.spfhe_ctx_destroy(g.ctx)
+
+
+def _dense_layer_few_matches():
+    """64x784 activations times 784x128 weights at the dense layer's ring with
+    three matches: (0, 0) aligns A by 2 slots and needs no final rotation,
+    (0, 1) sits at equal slots, (32, 3) aligns B by 1 slot and its final
+    rotation is the single base-16 digit 15 * 16^3 (t - min_pos = 4096)."""
+    A = np.zeros((64, 784))
+    W = np.zeros((784, 128))
+    A[0, 3], A[0, 9], A[0, 700], A[32, 50] = 0.6, 0.5, 0.25, 0.75
+    W[700, 0], W[9, 1], W[4, 2], W[6, 2], W[50, 3] = -0.06, 0.08, 0.03, 0.04, -0.05
+    return A, W
+
+
+def test_dense_layer_ring_bit_exact_few_matches():
+    """The dense layer's ring and launch configuration (N=2^17, L=35, dnum=5,
+    K=6, rotation base 16): ct x ct (Alg. 2), ct x pt (Alg. 2 with weight
+    plaintexts) and the lazy-accumulation ct x pt product the benchmark times
+    are each bit-identical to the oracle on a product with three matches, and
+    decrypt within 1e-4 of FP64."""
+    ckks.threads(os.cpu_count() or 1)
+    recipe = synthetic.ring_dense_layer()
+    A, W = _dense_layer_few_matches()
+    rows, cols = A.shape[0], W.shape[1]
+    Acsr = spmspm.dense_to_csr(A)
+    Bcsc = spmspm.dense_to_csc(W)
+    p = Pair(recipe, rot_base=16)
+    try:
+        o, P, sp = p.o, p.P, p.spfhe
+        assert (P.n, P.L, P.K) == (1 << 17, 35, 6)
+        amounts = set(spmspm.final_rotation_amounts(Acsr[:2], Bcsc[:2], rows, cols, P.slots))
+        # ct x pt rotates each product from A's slot to its target slot
+        for m in spmspm.alg1_matches(Acsr[0], Acsr[1], Bcsc[0], Bcsc[1], rows, cols):
+            amounts.add((m.a_pos % P.slots - (m.i * cols + m.j)) % P.slots)
+        steps = set()
+        for r in amounts:
+            steps.update(ckks.rotation_plan(r, P.slots, P.rot_base))
+        assert steps == {1, 2, 15 << 12}
+        keys = o.keygen(41, rot_amounts=sorted(steps))
+        gkeys = p.import_keys(keys)
+        rng = np.random.default_rng(42)
+        A_cts = [o.encrypt(o.encode(z, P.L, P.scale), keys, rng) for z in spmspm.pack_values(Acsr[2], P.slots)]
+        B_cts = [o.encrypt(o.encode(z, P.L, P.scale), keys, rng) for z in spmspm.pack_values(Bcsc[2], P.slots)]
+        gA = [p.import_ct(c) for c in A_cts]
+        gB = [p.import_ct(c) for c in B_cts]
+        Am = sp.sparse_meta(Acsr[0], Acsr[1], rows, A.shape[1])
+        Bm = sp.sparse_meta(Bcsc[0], Bcsc[1], W.shape[0], cols)
+        ref = A @ W
+
+        # ct x ct, Alg. 2 as printed
+        mask = spmspm.make_mask(o, 0, P.L - 1)
+        counts = spmspm.OpCounts()
+        want = spmspm.spmspm_ct_ct(o, keys, Acsr[:2], A_cts, Bcsc[:2], B_cts, rows, cols, mask_pt=mask,
+                                   counts=counts)
+        assert (counts.matches, counts.ks_align, counts.ks_final) == (3, 2, 1)
+        outs, st = sp.spfhe_sparse_matmul_ct_ct(p.ctx, gkeys, Am, gA, Bm, gB, p.import_pt(mask), 1)
+        p.track("ct", outs[0])
+        p.assert_ct_equal(outs[0], want[0])
+        assert st["ks_final"] == counts.ks_final and st["ks_align"] == counts.ks_align
+        assert np.max(np.abs(spmspm.decrypt_result(o, keys, want, rows, cols) - ref)) < 1e-4
+
+        # ct x pt: weight plaintexts encoded by the oracle, imported
+        Bd = Bcsc[2]
+        base = [o.encode_onehot(float(v), 0, P.L, spmspm.weight_scale(o)) for v in Bd]
+        gpts = [p.import_pt(b) for b in base]
+        counts = spmspm.OpCounts()
+        want = spmspm.spmspm_ct_pt(o, keys, Acsr[:2], A_cts, Bcsc[:2], Bd, rows, cols, b_pts=base, counts=counts)
+        outs, st = sp.spfhe_sparse_matmul_ct_pt(p.ctx, gkeys, Am, gA, Bm, None, gpts, 1)
+        p.track("ct", outs[0])
+        p.assert_ct_equal(outs[0], want[0])
+        assert st["ks_final"] == counts.ks_final
+        assert np.max(np.abs(spmspm.decrypt_result(o, keys, want, rows, cols) - ref)) < 1e-4
+
+        # the lazy-accumulation ct x pt product (the benchmark's dense-layer path)
+        counts = spmspm.OpCounts()
+        want = spmspm.spmspm_ct_pt_grouped(o, keys, Acsr[:2], A_cts, Bcsc[:2], Bd, rows, cols, b_pts=base,
+                                           merge_digits=True, counts=counts)
+        outs, st = sp.spfhe_sparse_matmul_ct_pt_grouped(p.ctx, gkeys, Am, gA, Bm, None, gpts, 1, merge_digits=True)
+        p.track("ct", outs[0])
+        p.assert_ct_equal(outs[0], want[0])
+        for k in ("matches", "ks_final", "rescales"):
+            assert st[k] == getattr(counts, k), k
+        assert np.max(np.abs(spmspm.decrypt_result(o, keys, want, rows, cols) - ref)) < 1e-4
+    finally:
+        p.close()

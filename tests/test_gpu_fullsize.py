@@ -2,7 +2,10 @@
 256) and launch configuration: a 128x128 product crafted to have a few
 matches (the oracle needs tens of seconds per key switch at this size) is
 bit-identical to the oracle, and the full 128x128 workload product decrypts
-within 1e-4 of FP64 (a property that holds at any size)."""
+within 1e-4 of FP64 (a property that holds at any size).  At the dense
+layer's ring (N=2^17, L=35, dnum=5, K=6, rotation base 16) a 64x784 x 784x128
+product with three matches is bit-identical to the oracle through ct x ct,
+ct x pt and the lazy-accumulation ct x pt product."""
 import os
 
 import numpy as np

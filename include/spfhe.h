@@ -194,6 +194,23 @@ spfhe_status spfhe_keygen(spfhe_ctx *ctx, uint64_t seed, spfhe_keys **out);
 spfhe_status spfhe_keys_import(spfhe_ctx *ctx, const int64_t *secret, const uint64_t *relin,
                                size_t n_rot, const int32_t *rot_amounts, const uint64_t *const *rot,
                                spfhe_keys **out);
+/* Checkpoint of a key set: writes what spfhe_keys_import takes back, so keys
+ * made by spfhe_keygen survive the process or move to another context with
+ * the same parameters.  The paper describes no key storage; it notes that
+ * switching keys take hundreds of MB each (Sec. 1), which is what a restart
+ * would otherwise regenerate.  secret: n int64
+ * coefficients in {-1, 0, 1}, or NULL.  relin: [dnum][2][L+K][n] uint64,
+ * evaluation representation (the import layout), or NULL.  Rotation keys:
+ * with rot_amounts = NULL only their count is written to *n_rot; otherwise
+ * *n_rot gives the room in rot_amounts (int32, written in ascending order)
+ * and rot (NULL, or *n_rot pointers, each NULL or a buffer of the relin
+ * layout), and receives the count.  Buffers may be host or device memory;
+ * the call synchronises the context stream.  Errors: SPFHE_EINVAL (null
+ * ctx/keys/n_rot, keys of another context, room for fewer keys than the set
+ * holds), SPFHE_EKEY (relin requested from a set imported without one),
+ * SPFHE_ENOMEM, SPFHE_ECUDA. */
+spfhe_status spfhe_keys_export(spfhe_ctx *ctx, const spfhe_keys *keys, int64_t *secret, uint64_t *relin,
+                               size_t *n_rot, int32_t *rot_amounts, uint64_t *const *rot);
 void spfhe_keys_free(spfhe_keys *keys);
 
 /* ---- plaintexts --------------------------------------------------------- */

@@ -260,6 +260,18 @@ spfhe_status spfhe_keys_import(spfhe_ctx *ctx, const int64_t *secret, const uint
     });
 }
 
+spfhe_status spfhe_keys_export(spfhe_ctx *ctx, const spfhe_keys *keys, int64_t *secret, uint64_t *relin,
+                               size_t *n_rot, int32_t *rot_amounts, uint64_t *const *rot)
+{
+    return guard([&] {
+        need(keys && n_rot, "null argument");
+        Ctx &c = C(ctx);
+        need(keys->k->ctx == &c, "the key set belongs to another context");
+        keys_export(c, *keys->k, secret, reinterpret_cast<u64 *>(relin), n_rot, rot_amounts,
+                    reinterpret_cast<u64 *const *>(rot));
+    });
+}
+
 void spfhe_keys_free(spfhe_keys *keys)
 {
     if (!keys) return;

@@ -136,6 +136,7 @@ struct Keys {
     u64 *s = nullptr;                // secret, evaluation rep. over all M moduli, Montgomery form
     u64 *relin = nullptr;            // [dnum][2][M][n], Montgomery form
     std::map<int, u64 *> rot;        // amount -> [dnum][2][M][n], Montgomery form
+    std::vector<long long> s_coef;   // host copy of the ternary secret (coefficients), for export
     size_t key_words() const;
 };
 

@@ -103,6 +103,7 @@ void accumulate(Ctx &ctx, int ell, u64 *result, const u64 *x, long long stride, 
 void add_ct(Ctx &ctx, int polys, int ell, const u64 *a, const u64 *b, u64 *out);
 void mul_ct_pt(Ctx &ctx, int ell, const u64 *ct, const u64 *pt, u64 *out);           // pt standard form
 void to_montgomery(Ctx &ctx, u64 *x, int limbs, const int *mi_host, int reps);         // in place
+void from_montgomery(Ctx &ctx, u64 *x, int limbs, const int *mi_host, int reps);       // in place, x 2^-64
 void from_signed(Ctx &ctx, const long long *coef, u64 *out, int limbs);                // out[l] = coef mod q_l
 void decrypt_core(Ctx &ctx, int ell, const u64 *ct, const u64 *s_mont, u64 *out);      // c0 + c1 s
 void copy_words(Ctx &ctx, u64 *dst, const u64 *src, size_t words);

@@ -70,6 +70,9 @@ Keys *keygen(Ctx &ctx, uint64_t seed)
         u64 *s_std = sc.words((size_t)M * n);
         u64 *sp = sc.words((size_t)M * n);
         sample_ternary(ctx, sc_coef, seed, 1);
+        k->s_coef.resize(n);
+        SPFHE_CHECK_CUDA(cudaMemcpyAsync(k->s_coef.data(), sc_coef, n * sizeof(long long), cudaMemcpyDeviceToHost,
+                                         ctx.stream));
         from_signed(ctx, sc_coef, s_std, M);
         ntt_forward(ctx, Batch{s_std, 0, 1, nullptr}, limb_range(0, M, 0));
         k->s = static_cast<u64 *>(dev_alloc(ctx, (size_t)M * n * sizeof(u64)));
@@ -122,6 +125,7 @@ Keys *keys_import(Ctx &ctx, const int64_t *secret, const u64 *relin, size_t n_ro
         std::vector<int> mi = all_moduli(ctx);
         for (size_t i = 0; i < n; ++i)
             if (secret[i] < -1 || secret[i] > 1) throw Error(SPFHE_EINVAL, "secret must be ternary");
+        k->s_coef.assign(secret, secret + n);
         Scratch sc(ctx);
         long long *coef = sc.typed<long long>(n);
         SPFHE_CHECK_CUDA(cudaMemcpyAsync(coef, secret, n * sizeof(long long), cudaMemcpyHostToDevice, ctx.stream));
@@ -150,6 +154,44 @@ Keys *keys_import(Ctx &ctx, const int64_t *secret, const u64 *relin, size_t n_ro
         throw;
     }
     return k;
+}
+
+// The inverse of keys_import: the ternary secret and every switching key in
+// standard (not Montgomery) evaluation form, each key converted in a scratch
+// copy on the device and copied to the caller's host or device buffer.
+void keys_export(Ctx &ctx, const Keys &k, int64_t *secret, u64 *relin, size_t *n_rot, int32_t *amounts,
+                 u64 *const *rot)
+{
+    const size_t n = ctx.n, kw = k.key_words();
+    if (amounts && *n_rot < k.rot.size())
+        throw Error(SPFHE_EINVAL, "room for " + std::to_string(*n_rot) + " rotation keys, the key set holds " +
+                                      std::to_string(k.rot.size()));
+    if (relin && !k.relin) throw Error(SPFHE_EKEY, "the key set holds no relinearisation key");
+    if (secret) {
+        if (k.s_coef.size() != n) throw Error(SPFHE_EINVAL, "the key set holds no secret coefficients");
+        for (size_t i = 0; i < n; ++i) secret[i] = (int64_t)k.s_coef[i];
+    }
+    std::vector<int> mi = all_moduli(ctx);
+    Scratch sc(ctx);
+    u64 *tmp = (relin || (amounts && rot)) ? sc.words(kw) : nullptr;
+    auto put = [&](const u64 *key, u64 *dst) {
+        SPFHE_CHECK_CUDA(cudaMemcpyAsync(tmp, key, kw * sizeof(u64), cudaMemcpyDeviceToDevice, ctx.stream));
+        from_montgomery(ctx, tmp, ctx.M, mi.data(), 2 * ctx.dnum);
+        SPFHE_CHECK_CUDA(cudaMemcpyAsync(dst, tmp, kw * sizeof(u64), cudaMemcpyDefault, ctx.stream));
+        // tmp is reused by the next key: this copy must have landed first
+        SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+    };
+    if (relin) put(k.relin, relin);
+    if (amounts) {
+        size_t i = 0;
+        for (const auto &kv : k.rot) {
+            amounts[i] = kv.first;
+            if (rot && rot[i]) put(kv.second, rot[i]);
+            ++i;
+        }
+    }
+    *n_rot = k.rot.size();
+    SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
 }
 
 Ct *ct_new(Ctx &ctx, int level, double scale)

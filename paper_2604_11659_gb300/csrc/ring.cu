@@ -436,6 +436,17 @@ __global__ void k_to_mont(int n, u64 *x, MiList ml, int limbs, const ModConst *_
     *p = to_mont(*p, m);
 }
 
+// x -> x 2^-64 mod q (out of Montgomery form), x < q
+__global__ void k_from_mont(int n, u64 *x, MiList ml, int limbs, const ModConst *__restrict__ mc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int l = blockIdx.y, rep = blockIdx.z;
+    const ModConst m = mc[ml.mi[l]];
+    u64 *p = x + ((size_t)rep * limbs + l) * n + k;
+    *p = redc(U128{*p, 0}, m.q, m.qneg_inv);
+}
+
 __global__ void k_from_signed(int n, const long long *coef, u64 *out, const ModConst *__restrict__ mc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -907,6 +918,17 @@ void to_montgomery(Ctx &ctx, u64 *x, int limbs, const int *mi_host, int reps)
         cudaEvent_t t0_ = prof_begin(ctx);
         k_to_mont<<<grid_n(ctx.n, limbs, reps), kT, 0, ctx.stream>>>(ctx.n, x, ml, limbs, ctx.dt.mc);
         prof_end(ctx, t0_, K_OTHER, 16.0 * ctx.n * limbs * reps, 1.0 * ctx.n * limbs * reps, "to montgomery");
+    }
+}
+
+void from_montgomery(Ctx &ctx, u64 *x, int limbs, const int *mi_host, int reps)
+{
+    MiList ml;
+    for (int l = 0; l < limbs; ++l) ml.mi[l] = mi_host[l];
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_from_mont<<<grid_n(ctx.n, limbs, reps), kT, 0, ctx.stream>>>(ctx.n, x, ml, limbs, ctx.dt.mc);
+        prof_end(ctx, t0_, K_OTHER, 16.0 * ctx.n * limbs * reps, 1.0 * ctx.n * limbs * reps, "from montgomery");
     }
 }
 

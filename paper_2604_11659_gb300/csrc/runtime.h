@@ -87,6 +87,8 @@ std::vector<int> plan_key_amounts(const Ctx &ctx);
 Keys *keygen(Ctx &ctx, uint64_t seed);
 Keys *keys_import(Ctx &ctx, const int64_t *secret, const u64 *relin, size_t n_rot, const int32_t *amounts,
                   const u64 *const *rot);
+void keys_export(Ctx &ctx, const Keys &k, int64_t *secret, u64 *relin, size_t *n_rot, int32_t *amounts,
+                 u64 *const *rot);
 void free_keys(Keys *k);
 Ct *ct_new(Ctx &ctx, int level, double scale);
 Pt *pt_new(Ctx &ctx, int level, double scale);

@@ -77,6 +77,8 @@ _SIGS = [
     ("spfhe_keygen", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
     ("spfhe_keys_import", ctypes.c_int, [handle, c_i64p, c_u64p, ctypes.c_size_t, c_i32p,
                                          ctypes.POINTER(c_u64p), ctypes.POINTER(handle)]),
+    ("spfhe_keys_export", ctypes.c_int, [handle, handle, c_i64p, c_u64p, ctypes.POINTER(ctypes.c_size_t), c_i32p,
+                                         ctypes.POINTER(c_u64p)]),
     ("spfhe_keys_free", None, [handle]),
     ("spfhe_encode", ctypes.c_int, [handle, c_dblp, c_dblp, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double,
                                     ctypes.POINTER(handle)]),
@@ -308,6 +310,21 @@ def spfhe_keys_import(ctx, secret: np.ndarray, relin: np.ndarray, rot: dict):
     _check(lib().spfhe_keys_import(ctx, secret.ctypes.data_as(c_i64p), _u64(relin), len(arrs), _i32(amts),
                                    ptrs, ctypes.byref(out)))
     return out
+
+
+def spfhe_keys_export(ctx, keys, n: int, key_shape):
+    """Returns (secret, relin, {amount: key}) in the layout spfhe_keys_import
+    takes; key_shape = (dnum, 2, L + K, n)."""
+    count = ctypes.c_size_t(0)
+    _check(lib().spfhe_keys_export(ctx, keys, None, None, ctypes.byref(count), None, None))
+    secret = np.empty(n, dtype=np.int64)
+    relin = np.empty(key_shape, dtype=np.uint64)
+    amts = np.empty(max(1, count.value), dtype=np.int32)
+    arrs = [np.empty(key_shape, dtype=np.uint64) for _ in range(count.value)]
+    ptrs = (c_u64p * max(1, len(arrs)))(*[_u64(a) for a in arrs])
+    _check(lib().spfhe_keys_export(ctx, keys, secret.ctypes.data_as(c_i64p), _u64(relin), ctypes.byref(count),
+                                   _i32(amts), ptrs))
+    return secret, relin, {int(a): k for a, k in zip(amts[: count.value], arrs)}
 
 
 def spfhe_keys_free(keys):

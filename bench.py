@@ -94,6 +94,26 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+NTT_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv"}
+
+
+def alu_microbench(meas, achieved_bfly, sm_mhz, sms=152):
+    """The library's measured ALU speed of light beside the derived peak:
+    butterflies/s of register-resident lazy forward butterflies (the
+    transforms' own Shoup arithmetic, no memory traffic), and the 32-bit
+    multiply-add rates per SM per clock that calibrate the derivation."""
+    if meas is None:
+        return None
+    bfly, imad, wide = meas
+    clk = sms * sm_mhz * 1e6
+    out = {"butterflies_per_s": bfly, "imad_per_s": imad, "imad_wide_per_s": wide,
+           "imad_per_clk_per_sm": imad / clk, "imad_wide_per_clk_per_sm": wide / clk,
+           "what": "register-resident microbenchmarks at 4 CTAs x 256 threads per SM (spfhe_prof_alu_peak)"}
+    if achieved_bfly is not None:
+        out["frac_of_butterfly_peak"] = achieved_bfly / bfly
+    return out
+
+
 class ClockSampler:
     def __init__(self, index: int):
         self.index = index
@@ -710,6 +730,13 @@ def main():
         g.free(outs)
     torch.cuda.synchronize()
 
+    # measured ALU speed of light (register-resident microbenchmarks), outside the timed region
+    try:
+        alu_meas = sp.spfhe_prof_alu_peak(g.ctx)
+    except sp.SpfheError as exc:
+        alu_meas = None
+        print("ALU microbenchmark unavailable: %s" % exc, file=sys.stderr)
+
     # timed region: device events on the context stream, per-kernel profile live
     sp.spfhe_prof_enable(g.ctx, True)
     launches0 = sp.spfhe_launch_count(g.ctx)
@@ -836,7 +863,9 @@ def main():
                 "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
                 "work_per_launch": dd["work"] / max(1, dd["launches"]),
                 "algorithmic_bytes_per_launch": dd["bytes"] / max(1, dd["launches"]),
-                "hbm_gbs": dd["bytes"] / (dd["ms"] * 1e-3) / 1e9}
+                "hbm_gbs": dd["bytes"] / (dd["ms"] * 1e-3) / 1e9,
+                "alu_microbench": alu_microbench(alu_meas, achieved if dom in NTT_CLASSES else None,
+                                                 clocks.get("sm_mhz") or sm_max)}
     else:
         achieved = dd["bytes"] / (dd["ms"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

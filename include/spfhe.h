@@ -176,6 +176,21 @@ const char *spfhe_prof_class_name(int cls);
  * output pair, and the switching key once per group of polynomials that
  * share it in one launch). */
 spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes);
+/* Measured arithmetic speed of light of the GPU behind ctx, the ALU roofline
+ * of the transforms and base conversions (64-bit modular arithmetic on the
+ * INT32 multiply pipe).  Three register-resident microbenchmarks run on the
+ * context stream with the transforms' launch shape (4 CTAs of 256 threads per
+ * SM, four waves), each timed with CUDA events after one warm-up launch and
+ * a few milliseconds long: lazy forward NTT butterflies with the transforms'
+ * truncated-quotient Shoup product (butterflies per second), and independent
+ * chains of 32-bit multiply-adds with a 32-bit (mad.lo) and a 64-bit
+ * (mad.wide) result (operations per second).  No memory traffic beyond one
+ * store per thread.  A measurement aid: the paper times wall-clock runs
+ * only (Sec. 4) and has no counterpart.  Any out-pointer may be NULL;
+ * synchronises the stream.  Errors: SPFHE_EINVAL (null ctx, called during
+ * graph capture), SPFHE_ENOMEM, SPFHE_ECUDA. */
+spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *imad_per_s,
+                                 double *imad_wide_per_s);
 
 /* ---- keys ------------------------------------------------------------ */
 /* Sample a ternary secret, the relinearisation key and one rotation key per

@@ -1,0 +1,174 @@
+// Measured arithmetic speed of light for the ALU-bound kernels.
+//
+// The transforms and base conversions are bound by 64-bit modular
+// multiplication on the INT32 multiply pipe, so their roofline is an ALU
+// rate, not a bandwidth.  These microbenchmarks measure that rate on the GPU
+// at hand, with the launch shape of the transforms (4 CTAs of 256 threads per
+// SM) and no memory traffic beyond one store per thread:
+//   * lazy forward butterflies (a, b) -> (a + w b, a - w b + 3q) on 8
+//     register-resident values per thread, three stages per round, with the
+//     transforms' truncated-quotient Shoup product (mul_shoup3);
+//   * independent chains of 32-bit multiply-adds with a 32-bit result
+//     (mad.lo.u32) and with a 64-bit result (mad.wide.u32).
+// Every launch runs a fixed number of rounds and touches only its own output
+// word, so it always ends and stays in bounds.
+#include "handles.h"
+#include "kernels.h"
+
+namespace spfhe {
+namespace {
+
+constexpr int kPeakThreads = 256;
+constexpr int kPeakCtasPerSm = 4;
+constexpr int kPeakWaves = 4;
+// butterfly benchmark: 8 values per thread, 3 stages (12 butterflies) per round
+constexpr int kBflyVals = 8;
+constexpr int kBflyStages = 3;
+
+__global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
+    k_peak_bfly(const u64 *__restrict__ seed, int rounds, u64 *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = seed[0], w = seed[1] + (u64)t, wp = seed[2] ^ (u64)t;
+    const u64 nq = 0 - q, q3 = 3 * q;
+    u64 v[kBflyVals];
+#pragma unroll
+    for (int i = 0; i < kBflyVals; ++i) v[i] = seed[3] + (u64)t * kBflyVals + (u64)i;
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int l = 0; l < kBflyStages; ++l) {
+            const int half = (kBflyVals / 2) >> l;
+#pragma unroll
+            for (int i = 0; i < kBflyVals; ++i) {
+                if (i & half) continue;
+                const u64 x = v[i];
+                const u64 y = mul_shoup3(v[i + half], w, wp, nq);
+                v[i] = x + y;
+                v[i + half] = x - y + q3;
+            }
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < kBflyVals; ++i) acc ^= v[i];
+    out[t] = acc;
+}
+
+__global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
+    k_peak_imad(const u64 *__restrict__ seed, int rounds, u64 *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = (uint32_t)seed[0] | 1u, c = (uint32_t)seed[1];
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (uint32_t)seed[3] + (uint32_t)(t * 8 + i);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) asm("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(m), "r"(c));
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= a[i];
+    out[t] = acc;
+}
+
+__global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
+    k_peak_imad_wide(const u64 *__restrict__ seed, int rounds, u64 *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = (uint32_t)seed[0] | 1u;
+    u64 a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = seed[3] + (u64)(t * 8 + i);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            // a = hi32(a) * m + a: each step's multiplicand depends on the last
+            const uint32_t x = (uint32_t)(a[i] >> 32);
+            asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(x), "r"(m));
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= a[i];
+    out[t] = acc;
+}
+
+// Device time of one launch of `launch` (after one untimed warm-up launch).
+template <typename F> double time_launch(Ctx &ctx, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    SPFHE_CHECK_CUDA(cudaEventCreate(&a));
+    const cudaError_t eb = cudaEventCreate(&b);
+    if (eb != cudaSuccess) {
+        cudaEventDestroy(a);
+        throw Error(SPFHE_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(eb));
+    }
+    float ms = 0;
+    cudaError_t e = cudaSuccess;
+    launch();
+    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(a, ctx.stream)) == cudaSuccess) {
+        launch();
+        if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(b, ctx.stream)) == cudaSuccess &&
+            (e = cudaEventSynchronize(b)) == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) throw Error(SPFHE_ECUDA, std::string("ALU microbenchmark: ") + cudaGetErrorString(e));
+    ctx.launches += 2;
+    return ms * 1e-3;
+}
+
+}  // namespace
+}  // namespace spfhe
+
+using namespace spfhe;
+
+extern "C" spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *imad_per_s,
+                                            double *imad_wide_per_s)
+{
+    try {
+        if (!ctx) throw Error(SPFHE_EINVAL, "null argument");
+        Ctx &c = ctx->c;
+        if (c.cap) throw Error(SPFHE_EINVAL, "not available during graph capture");
+        SPFHE_CHECK_CUDA(cudaSetDevice(c.device));
+        int sms = 0;
+        SPFHE_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+        const int blocks = sms * kPeakCtasPerSm * kPeakWaves;
+        const size_t threads = (size_t)blocks * kPeakThreads;
+        // the first modulus and a twiddle of it; the values only feed the arithmetic
+        const u64 q = c.mods[0];
+        const u64 w = q / 3 + 1;
+        const u64 wp = (u64)(((unsigned __int128)w << 64) / q);
+        const u64 seed_h[4] = {q, w, wp, 12345};
+        u64 *seed = static_cast<u64 *>(dev_alloc(c, sizeof(seed_h)));
+        u64 *out = nullptr;
+        try {
+            out = static_cast<u64 *>(dev_alloc(c, threads * sizeof(u64)));
+            SPFHE_CHECK_CUDA(cudaMemcpyAsync(seed, seed_h, sizeof(seed_h), cudaMemcpyHostToDevice, c.stream));
+            const int rb = 512, ri = 4096;
+            const double t_b = time_launch(c, [&] { k_peak_bfly<<<blocks, kPeakThreads, 0, c.stream>>>(seed, rb, out); });
+            const double t_i = time_launch(c, [&] { k_peak_imad<<<blocks, kPeakThreads, 0, c.stream>>>(seed, ri, out); });
+            const double t_w =
+                time_launch(c, [&] { k_peak_imad_wide<<<blocks, kPeakThreads, 0, c.stream>>>(seed, ri, out); });
+            if (butterflies_per_s) *butterflies_per_s = (double)threads * rb * kBflyStages * (kBflyVals / 2) / t_b;
+            if (imad_per_s) *imad_per_s = (double)threads * ri * 8 / t_i;
+            if (imad_wide_per_s) *imad_wide_per_s = (double)threads * ri * 8 / t_w;
+        } catch (...) {
+            dev_free(c, out);
+            dev_free(c, seed);
+            throw;
+        }
+        dev_free(c, out);
+        dev_free(c, seed);
+        SPFHE_CHECK_CUDA(cudaStreamSynchronize(c.stream));
+        return SPFHE_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return SPFHE_EINVAL;
+    }
+}

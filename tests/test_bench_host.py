@@ -22,3 +22,12 @@ def test_ks_ntt_fwd_traffic_without_fused_passes():
     got = bench.ks_ntt_fwd_traffic(work, 32.0 * n * la, 2, n, log_n)
     d = bench.NTT_FWD_DRAM_PER_LIMB
     assert abs(got - la * (d["a"] + d["b"]) / 2) < 1e-6 * got
+
+
+def test_alu_microbench_summary():
+    meas = (1.5e12, 2.0e13, 1.0e13)
+    out = bench.alu_microbench(meas, 0.75e12, 2070.0)
+    assert out["frac_of_butterfly_peak"] == 0.5
+    assert abs(out["imad_per_clk_per_sm"] - 2.0e13 / (152 * 2070e6)) < 1e-9
+    assert bench.alu_microbench(None, 1.0, 2070.0) is None
+    assert "frac_of_butterfly_peak" not in bench.alu_microbench(meas, None, 2070.0)

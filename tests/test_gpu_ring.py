@@ -199,3 +199,18 @@ def test_library_keygen_functional_and_noise(pair):
     assert np.max(np.abs(ec)) <= 19
     if pair.n >= 4096:
         assert 2.6 < np.std(ec) < 3.8
+
+
+def test_alu_peak_microbenchmarks():
+    """The measured ALU speed of light: positive rates in a plausible range,
+    and a lazy butterfly (nine 32-bit multiplies) slower than one 32-bit
+    multiply-add."""
+    sp = need_gpu()
+    from paper_2604_11659_gb300 import params as gparams
+    ctx = sp.spfhe_ctx_create(gparams.ctx_params(synthetic.ring_tiny(log_n=6, L=4, dnum=1, rot_base=2)))
+    try:
+        bfly, imad, wide = sp.spfhe_prof_alu_peak(ctx)
+        assert 1e10 < bfly < 1e14 and 1e11 < imad < 1e15 and 1e11 < wide < 1e15
+        assert bfly < imad / 4
+    finally:
+        sp.spfhe_ctx_destroy(ctx)

@@ -146,13 +146,15 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * with the register budget of 2 CTAs per SM; 2 = as 1, with the second pass
  * copying its twiddles into shared memory asynchronously before its data
  * loads (about 64 KB of dynamic shared memory per CTA); 3 = as 0 with the
- * register budget of 4 CTAs per SM.  EINVAL otherwise.
+ * register budget of 4 CTAs per SM; 4 = as 3 with every 32x32-bit partial
+ * product of the Shoup multiplications taken as separate low and high
+ * halves instead of one 64-bit-result multiply.  EINVAL otherwise.
  * Results do not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
 /* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
  * the rescale's spread and last step run inside the forward transforms that
- * feed them (kernel variant 0 or 3, n >= 2^12); 0: as separate kernels.  Results
+ * feed them (kernel variant 0, 3 or 4, n >= 2^12); 0: as separate kernels.  Results
  * do not depend on it. */
 spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable);
 
@@ -182,15 +184,17 @@ spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes
  * context stream with the transforms' launch shape (4 CTAs of 256 threads per
  * SM, four waves), each timed with CUDA events after one warm-up launch and
  * a few milliseconds long: lazy forward NTT butterflies with the transforms'
- * truncated-quotient Shoup product (butterflies per second), and independent
+ * truncated-quotient Shoup product, its partial products taken as 64-bit
+ * results (kernel variants 0-3) and as split 32-bit halves (variant 4)
+ * (butterflies per second), and independent
  * chains of 32-bit multiply-adds with a 32-bit (mad.lo) and a 64-bit
  * (mad.wide) result (operations per second).  No memory traffic beyond one
  * store per thread.  A measurement aid: the paper times wall-clock runs
  * only (Sec. 4) and has no counterpart.  Any out-pointer may be NULL;
  * synchronises the stream.  Errors: SPFHE_EINVAL (null ctx, called during
  * graph capture), SPFHE_ENOMEM, SPFHE_ECUDA. */
-spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *imad_per_s,
-                                 double *imad_wide_per_s);
+spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *butterflies_split_per_s,
+                                 double *imad_per_s, double *imad_wide_per_s);
 
 /* ---- keys ------------------------------------------------------------ */
 /* Sample a ternary secret, the relinearisation key and one rotation key per

@@ -195,7 +195,7 @@ spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {
         need(ctx != nullptr, "null context");
-        need(variant <= 3, "NTT variant must be 0 to 3");
+        need(variant <= 4, "NTT variant must be 0 to 4");
         ctx->c.ntt_variant = (int)variant;
     });
 }

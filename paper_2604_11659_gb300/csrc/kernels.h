@@ -18,7 +18,7 @@ struct Batch {
 void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map);
 
 // Forward transforms with a fused prologue or epilogue (radix-16 sizes,
-// kernel variant 0 or 3, no item list; returns false otherwise and does
+// kernel variant 0, 3 or 4, no item list; returns false otherwise and does
 // nothing):
 //   kFuseModDown: the transform of ModDown's conv [items][2][ell][n] writes
 //     out = base[sigma(k)] + (acc - conv) P^{-1} instead of conv;

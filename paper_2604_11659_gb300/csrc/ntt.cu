@@ -263,7 +263,7 @@ __device__ __forceinline__ void r16_load_tw(ulonglong2 (&wt)[16], int t, const u
 // all values by 3q, so after the log_n <= 17 stages of both passes they lie
 // in [0, 52q) (< 2^64) and pass B reduces them once at the end.  Otherwise
 // values stay in [0, 6q): x is first brought to [0, 3q).
-template <int P, int RND, int l, bool LAZY, bool SM>
+template <int P, int RND, int l, bool LAZY, bool SM, bool SPL = false>
 __device__ __forceinline__ void r16_fwd_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt, int ltile)
 {
@@ -277,14 +277,14 @@ __device__ __forceinline__ void r16_fwd_stage(u64 (&v)[16], int t, const ulonglo
         if (i & half) continue;
         const ulonglong2 w = wt[i >> (Q - l)];
         const u64 x = LAZY ? v[i] : csub(v[i], q3);
-        const u64 y = mul_shoup3(v[i + half], w.x, w.y, nq);
+        const u64 y = mul_shoup3v<SPL>(v[i + half], w.x, w.y, nq);
         v[i] = x + y;
         v[i + half] = x - y + q3;
     }
 }
 
 // PRE: the stage's twiddles were loaded ahead into `pre`
-template <int P, int RND, int l, bool SM, bool PRE = false>
+template <int P, int RND, int l, bool SM, bool PRE = false, bool SPL = false>
 __device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt, int ltile,
                                               const ulonglong2 (*pre)[16] = nullptr)
@@ -305,39 +305,39 @@ __device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglo
         const ulonglong2 w = wt[i >> (Q - l)];
         const u64 x = v[i], y = v[i + half];
         v[i] = csub(x + y, q3);
-        v[i + half] = mul_shoup3(x - y + q3, w.x, w.y, nq);
+        v[i + half] = mul_shoup3v<SPL>(x - y + q3, w.x, w.y, nq);
     }
 }
 
 // Lazy butterflies (Harvey's scheme with the [0, 3q) products of
 // mul_shoup3): forward values stay below 6q (52q on the reduction-free path),
 // inverse values in [0, 3q); only the last pass reduces to [0, q).
-template <int P, int RND, bool LAZY, bool SM = false>
+template <int P, int RND, bool LAZY, bool SM = false, bool SPL = false>
 __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt = nullptr,
                                               int ltile = 0)
 {
     constexpr int Q = r16_q<P, RND>();
-    r16_fwd_stage<P, RND, 0, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 1) r16_fwd_stage<P, RND, 1, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 2) r16_fwd_stage<P, RND, 2, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 3) r16_fwd_stage<P, RND, 3, LAZY, SM>(v, t, w2, q, stage0, btile, smt, ltile);
+    r16_fwd_stage<P, RND, 0, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 1) r16_fwd_stage<P, RND, 1, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 2) r16_fwd_stage<P, RND, 2, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 3) r16_fwd_stage<P, RND, 3, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
 }
 
 // moduli below this take the reduction-free forward butterflies
 constexpr u64 kLazyFwdBound = 1ull << 58;
 
 // PRE: the twiddles of the round's first stage (l = Q - 1) are in `pre`
-template <int P, int RND, bool SM = false, bool PRE = false>
+template <int P, int RND, bool SM = false, bool PRE = false, bool SPL = false>
 __device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt = nullptr,
                                               int ltile = 0, const ulonglong2 (*pre)[16] = nullptr)
 {
     constexpr int Q = r16_q<P, RND>();
-    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM, PRE>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM, PRE && Q == 3>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM, PRE && Q == 2>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    r16_inv_stage<P, RND, 0, SM, PRE && Q == 1>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM, PRE, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM, PRE && Q == 3, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM, PRE && Q == 2, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    r16_inv_stage<P, RND, 0, SM, PRE && Q == 1, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
 }
 
 // shared-memory slot of tile element j (pass B layout; pad one word per 16)
@@ -357,8 +357,12 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 //   0: twiddles loaded per stage from global memory, 3 CTAs per SM;
 //   1: the same with the register budget of 2 CTAs per SM;
 //   2: as 1, and pass B copies its CTA's twiddles into shared memory with
-//      asynchronous copies issued before its data loads.
-template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V == 3 ? 4 : 2); }
+//      asynchronous copies issued before its data loads;
+//   3: as 0 with the register budget of 4 CTAs per SM;
+//   4: as 3 with the Shoup products split into single-word halves
+//      (mul_shoup3s; the same bits).
+template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V == 3 || V == 4 ? 4 : 2); }
+template <int V> constexpr bool r16_split() { return V == 4; }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -383,7 +387,7 @@ __device__ __forceinline__ void r16_prefetch_wait()
     __syncthreads();
 }
 
-template <int P, bool LAZY, int MODE>
+template <int P, bool LAZY, int MODE, bool SPL = false>
 __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n,
                                              const FuseArgs &f, const ModConst *__restrict__ mc)
 {
@@ -411,14 +415,14 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
     }
-    r16_fwd_round<P, 0, LAZY>(v, t, w2, q, 0, 0);
+    r16_fwd_round<P, 0, LAZY, false, SPL>(v, t, w2, q, 0, 0);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1, LAZY>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 1, LAZY, false, SPL>(v, t, w2, q, 0, 0);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -427,7 +431,7 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2, LAZY>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 2, LAZY, false, SPL>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
@@ -444,11 +448,12 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
-    if (q < kLazyFwdBound) fwd16_a_body<P, true, MODE>(sm, p, q, w2, log_n, f, mc);
-    else fwd16_a_body<P, false, MODE>(sm, p, q, w2, log_n, f, mc);
+    constexpr bool SPL = r16_split<V>();
+    if (q < kLazyFwdBound) fwd16_a_body<P, true, MODE, SPL>(sm, p, q, w2, log_n, f, mc);
+    else fwd16_a_body<P, false, MODE, SPL>(sm, p, q, w2, log_n, f, mc);
 }
 
-template <int P, bool LAZY, bool SM, int MODE = kFuseNone>
+template <int P, bool LAZY, bool SM, int MODE = kFuseNone, bool SPL = false>
 __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m, const ulonglong2 *__restrict__ w2,
                                              int PA, const ulonglong2 *smt, const FuseArgs &f = FuseArgs{},
                                              int log_n = 0)
@@ -464,14 +469,14 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = tp[r16_index<P, 0>(t, i)];
     if constexpr (SM) r16_prefetch_wait();
-    r16_fwd_round<P, 0, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
+    r16_fwd_round<P, 0, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
+        r16_fwd_round<P, 1, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -480,7 +485,7 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2, LAZY, SM>(v, t, w2, q, PA, btile, smt, tile);
+        r16_fwd_round<P, 2, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
     }
     // the last round holds 16 contiguous elements per thread: stage through
     // shared memory so the global stores are coalesced
@@ -556,16 +561,17 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
+    constexpr bool SPL = r16_split<V>();
     if constexpr (MODE != kFuseNone) {
-        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, MODE>(sm, p, m, w2, PA, nullptr, f, log_n);
-        else fwd16_b_body<P, false, false, MODE>(sm, p, m, w2, PA, nullptr, f, log_n);
+        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, MODE, SPL>(sm, p, m, w2, PA, nullptr, f, log_n);
+        else fwd16_b_body<P, false, false, MODE, SPL>(sm, p, m, w2, PA, nullptr, f, log_n);
     } else if constexpr (V == 2) {
         r16_prefetch_tw<P>(smt, w2, PA, (int)(((size_t)blockIdx.x * kElems) >> P));
         if (m.q < kLazyFwdBound) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
         else fwd16_b_body<P, false, true>(sm, p, m, w2, PA, smt);
     } else {
-        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false>(sm, p, m, w2, PA, nullptr);
-        else fwd16_b_body<P, false, false>(sm, p, m, w2, PA, nullptr);
+        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, kFuseNone, SPL>(sm, p, m, w2, PA, nullptr);
+        else fwd16_b_body<P, false, false, kFuseNone, SPL>(sm, p, m, w2, PA, nullptr);
     }
 }
 
@@ -577,6 +583,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     __shared__ u64 sm[r16_smem_words_b<P>()];
     extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
     constexpr bool SM = V == 2;
+    constexpr bool SPL = r16_split<V>();
     constexpr int TPT = 1 << (P - 4);
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
-    r16_inv_round<P, R - 1, SM, !SM>(v, t, w2, q, PA, btile, smt, tile, &wpre);
+    r16_inv_round<P, R - 1, SM, !SM, SPL>(v, t, w2, q, PA, btile, smt, tile, &wpre);
     if constexpr (R > 2) {
         __syncthreads();
 #pragma unroll
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2, SM>(v, t, w2, q, PA, btile, smt, tile);
+        r16_inv_round<P, R - 2, SM, false, SPL>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 1) {
         __syncthreads();
@@ -627,7 +634,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0, SM>(v, t, w2, q, PA, btile, smt, tile);
+        r16_inv_round<P, 0, SM, false, SPL>(v, t, w2, q, PA, btile, smt, tile);
     }
     u64 *tp = p + e0 + ((size_t)tile << P);
 #pragma unroll
@@ -650,17 +657,18 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
     const int lg_ncols = log_n - P;
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
+    constexpr bool SPL = r16_split<V>();
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol];
-    r16_inv_round<P, R - 1>(v, t, w2, q, 0, 0);
+    r16_inv_round<P, R - 1, false, false, SPL>(v, t, w2, q, 0, 0);
     if constexpr (R > 2) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, R - 1>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2>(v, t, w2, q, 0, 0);
+        r16_inv_round<P, R - 2, false, false, SPL>(v, t, w2, q, 0, 0);
         __syncthreads();
     }
     if constexpr (R > 1) {
@@ -669,7 +677,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0>(v, t, w2, q, 0, 0);
+        r16_inv_round<P, 0, false, false, SPL>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -715,7 +723,7 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variants 0 and 3)
+// transforms with a fused prologue / epilogue (kernel variants 0, 3 and 4)
 template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
@@ -731,12 +739,14 @@ template <int P, int V> struct R16FusedV {
 template <int P> struct R16Fused {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
+        if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_a(g, s, a, c, mode, f);
+        else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
         else R16FusedV<P, 0>::fwd_a(g, s, a, c, mode, f);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
+        if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_b(g, s, a, c, PA, mode, f);
+        else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
         else R16FusedV<P, 0>::fwd_b(g, s, a, c, PA, mode, f);
     }
 };
@@ -749,6 +759,7 @@ template <int P> struct R16Launch {
         case 1: f(R16LaunchV<P, 1>{}); break;
         case 2: f(R16LaunchV<P, 2>{}); break;
         case 3: f(R16LaunchV<P, 3>{}); break;
+        case 4: f(R16LaunchV<P, 4>{}); break;
         default: throw Error(SPFHE_EINVAL, "no such NTT variant");
         }
     }
@@ -910,7 +921,8 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
 
 bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f)
 {
-    if (ctx.log_n < 12 || (ctx.ntt_variant != 0 && ctx.ntt_variant != 3) || b.ids) return false;
+    if (ctx.log_n < 12 || (ctx.ntt_variant != 0 && ctx.ntt_variant != 3 && ctx.ntt_variant != 4) || b.ids)
+        return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
     NttArgs a{b.base, b.stride, b.ids, map};

@@ -7,7 +7,8 @@
 // SM) and no memory traffic beyond one store per thread:
 //   * lazy forward butterflies (a, b) -> (a + w b, a - w b + 3q) on 8
 //     register-resident values per thread, three stages per round, with the
-//     transforms' truncated-quotient Shoup product (mul_shoup3);
+//     transforms' truncated-quotient Shoup product, both as five 64-bit-result
+//     multiplies (mul_shoup3) and as their split halves (mul_shoup3s);
 //   * independent chains of 32-bit multiply-adds with a 32-bit result
 //     (mad.lo.u32) and with a 64-bit result (mad.wide.u32).
 // Every launch runs a fixed number of rounds and touches only its own output
@@ -25,6 +26,7 @@ constexpr int kPeakWaves = 4;
 constexpr int kBflyVals = 8;
 constexpr int kBflyStages = 3;
 
+template <bool SPL>
 __global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
     k_peak_bfly(const u64 *__restrict__ seed, int rounds, u64 *out)
 {
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(kPeakThreads, kPeakCtasPerSm)
             for (int i = 0; i < kBflyVals; ++i) {
                 if (i & half) continue;
                 const u64 x = v[i];
-                const u64 y = mul_shoup3(v[i + half], w, wp, nq);
+                const u64 y = mul_shoup3v<SPL>(v[i + half], w, wp, nq);
                 v[i] = x + y;
                 v[i + half] = x - y + q3;
             }
@@ -125,7 +127,8 @@ template <typename F> double time_launch(Ctx &ctx, F &&launch)
 
 using namespace spfhe;
 
-extern "C" spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *imad_per_s,
+extern "C" spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s,
+                                            double *butterflies_split_per_s, double *imad_per_s,
                                             double *imad_wide_per_s)
 {
     try {
@@ -148,11 +151,16 @@ extern "C" spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_
             out = static_cast<u64 *>(dev_alloc(c, threads * sizeof(u64)));
             SPFHE_CHECK_CUDA(cudaMemcpyAsync(seed, seed_h, sizeof(seed_h), cudaMemcpyHostToDevice, c.stream));
             const int rb = 512, ri = 4096;
-            const double t_b = time_launch(c, [&] { k_peak_bfly<<<blocks, kPeakThreads, 0, c.stream>>>(seed, rb, out); });
+            const double t_b =
+                time_launch(c, [&] { k_peak_bfly<false><<<blocks, kPeakThreads, 0, c.stream>>>(seed, rb, out); });
+            const double t_s =
+                time_launch(c, [&] { k_peak_bfly<true><<<blocks, kPeakThreads, 0, c.stream>>>(seed, rb, out); });
             const double t_i = time_launch(c, [&] { k_peak_imad<<<blocks, kPeakThreads, 0, c.stream>>>(seed, ri, out); });
             const double t_w =
                 time_launch(c, [&] { k_peak_imad_wide<<<blocks, kPeakThreads, 0, c.stream>>>(seed, ri, out); });
-            if (butterflies_per_s) *butterflies_per_s = (double)threads * rb * kBflyStages * (kBflyVals / 2) / t_b;
+            const double bflies = (double)threads * rb * kBflyStages * (kBflyVals / 2);
+            if (butterflies_per_s) *butterflies_per_s = bflies / t_b;
+            if (butterflies_split_per_s) *butterflies_split_per_s = bflies / t_s;
             if (imad_per_s) *imad_per_s = (double)threads * ri * 8 / t_i;
             if (imad_wide_per_s) *imad_wide_per_s = (double)threads * ri * 8 / t_w;
         } catch (...) {

@@ -74,7 +74,7 @@ _SIGS = [
     ("spfhe_prof_classes", ctypes.c_int, []),
     ("spfhe_prof_keyswitch", ctypes.c_int, [handle, ctypes.POINTER(ctypes.c_uint64), c_dblp]),
     ("spfhe_prof_class_name", ctypes.c_char_p, [ctypes.c_int]),
-    ("spfhe_prof_alu_peak", ctypes.c_int, [handle, c_dblp, c_dblp, c_dblp]),
+    ("spfhe_prof_alu_peak", ctypes.c_int, [handle, c_dblp, c_dblp, c_dblp, c_dblp]),
     ("spfhe_keygen", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
     ("spfhe_keys_import", ctypes.c_int, [handle, c_i64p, c_u64p, ctypes.c_size_t, c_i32p,
                                          ctypes.POINTER(c_u64p), ctypes.POINTER(handle)]),
@@ -292,10 +292,11 @@ def spfhe_prof_keyswitch(ctx):
 
 
 def spfhe_prof_alu_peak(ctx):
-    """(butterflies/s, mad.lo ops/s, mad.wide ops/s) measured on the GPU."""
-    b, i, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _check(lib().spfhe_prof_alu_peak(ctx, ctypes.byref(b), ctypes.byref(i), ctypes.byref(w)))
-    return b.value, i.value, w.value
+    """(butterflies/s, split-product butterflies/s, mad.lo ops/s, mad.wide
+    ops/s) measured on the GPU."""
+    b, bs, i, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().spfhe_prof_alu_peak(ctx, ctypes.byref(b), ctypes.byref(bs), ctypes.byref(i), ctypes.byref(w)))
+    return b.value, bs.value, i.value, w.value
 
 
 def spfhe_prof_all(ctx) -> dict:

@@ -25,9 +25,10 @@ def test_ks_ntt_fwd_traffic_without_fused_passes():
 
 
 def test_alu_microbench_summary():
-    meas = (1.5e12, 2.0e13, 1.0e13)
+    meas = (1.5e12, 1.2e12, 2.0e13, 1.0e13)
     out = bench.alu_microbench(meas, 0.75e12, 2070.0)
     assert out["frac_of_butterfly_peak"] == 0.5
+    assert bench.alu_microbench((1.0e12, 1.5e12, 2.0e13, 1.0e13), 0.75e12, 2070.0)["frac_of_butterfly_peak"] == 0.5
     assert abs(out["imad_per_clk_per_sm"] - 2.0e13 / (152 * 2070e6)) < 1e-9
     assert bench.alu_microbench(None, 1.0, 2070.0) is None
     assert "frac_of_butterfly_peak" not in bench.alu_microbench(meas, None, 2070.0)

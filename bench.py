@@ -38,6 +38,19 @@ NTT_FWD_DRAM_PER_LIMB = {"a": (151.2e6 + 90.8e6) / 288, "b": (250.2e6 + 138.6e6)
                          "b_moddown": (456.6e6 + 150.7e6) / 288}
 
 
+# kernel variant those captures were taken on: traffic is reported only for it
+NTT_FWD_DRAM_VARIANT = 3
+
+
+def traffic_source(dom, variant):
+    if dom != "ks_ntt_fwd":
+        return "no DRAM counters for this kernel class"
+    if variant != NTT_FWD_DRAM_VARIANT:
+        return ("null: DRAM counters were captured on kernel variant %d, the tuner ran variant %d"
+                % (NTT_FWD_DRAM_VARIANT, variant))
+    return "ncu DRAM bytes per limb of the profiler case, scaled to the launch's limbs by pass kind"
+
+
 def ks_ntt_fwd_traffic(work, nbytes, launches, n, log_n):
     """DRAM bytes per launch of the key-switching forward transforms.  The
     class's limbs are split by pass kind from its totals: every limb costs
@@ -861,7 +874,8 @@ def main():
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tmulmod/s", "frac": achieved / peak,
                 "traffic": (ks_ntt_fwd_traffic(dd["work"], dd["bytes"], dd["launches"], g.n, g.rec.log_n)
-                            if dom == "ks_ntt_fwd" else None),
+                            if dom == "ks_ntt_fwd" and g.ntt_chunk[0] == NTT_FWD_DRAM_VARIANT else None),
+                "traffic_source": traffic_source(dom, g.ntt_chunk[0]),
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
                 "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
                 "work_per_launch": dd["work"] / max(1, dd["launches"]),

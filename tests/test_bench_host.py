@@ -32,3 +32,9 @@ def test_alu_microbench_summary():
     assert abs(out["imad_per_clk_per_sm"] - 2.0e13 / (152 * 2070e6)) < 1e-9
     assert bench.alu_microbench(None, 1.0, 2070.0) is None
     assert "frac_of_butterfly_peak" not in bench.alu_microbench(meas, None, 2070.0)
+
+
+def test_traffic_only_for_the_captured_variant():
+    assert "variant 3, the tuner ran variant 4" in bench.traffic_source("ks_ntt_fwd", 4)
+    assert bench.traffic_source("ks_ntt_fwd", bench.NTT_FWD_DRAM_VARIANT).startswith("ncu")
+    assert bench.traffic_source("modup_bconv", 3).startswith("no DRAM")

@@ -38,3 +38,24 @@ def test_traffic_only_for_the_captured_variant():
     assert "variant 3, the tuner ran variant 4" in bench.traffic_source("ks_ntt_fwd", 4)
     assert bench.traffic_source("ks_ntt_fwd", bench.NTT_FWD_DRAM_VARIANT).startswith("ncu")
     assert bench.traffic_source("modup_bconv", 3).startswith("no DRAM")
+
+
+def test_check_reports_max_abs_and_frobenius_errors():
+    """GpuMatmul.check on a stub library: the decoded slots hold A B plus a
+    known error, and both error measures come out of it."""
+    import types
+
+    import numpy as np
+    A = np.array([[1.0, 0.0], [0.5, 2.0]])
+    B = np.array([[0.0, 1.0], [1.0, 0.0]])
+    err = np.array([3e-7, -4e-7, 0.0, 0.0])
+    S = 8
+    slots = np.zeros(S)
+    slots[:4] = (A @ B).reshape(-1) + err
+    sp = types.SimpleNamespace(spfhe_decrypt=lambda ctx, keys, h: h, spfhe_pt_free=lambda pt: None,
+                               spfhe_decode=lambda ctx, pt, n: slots[:n].astype(complex))
+    g = bench.GpuMatmul.__new__(bench.GpuMatmul)
+    g.sp, g.ctx, g.keys, g.S, g.rows, g.cols = sp, None, None, S, 2, 2
+    g.case = types.SimpleNamespace(A=A, B=B)
+    assert abs(g.check(["chunk"]) - 4e-7) < 1e-15
+    assert abs(g.last_frobenius - 5e-7) < 1e-15

@@ -62,3 +62,54 @@ def test_planner_rejects_malformed_metadata(sp):
         assert e.value.status == -1
     with pytest.raises(sp.SpfheError):
         sp.spfhe_plan_matches(good, sp.sparse_meta(ip, ix, 3, 2))   # inner dims differ
+
+
+def _plan_key_switches(A, B, S, base):
+    """Key switches of Alg. 1 + Alg. 2's rotations for one rotation base,
+    counted from the oracle's planner and rotation plan: each distinct
+    alignment (operand, chunk, amount) once, every final rotation."""
+    from oracle import ckks
+    Aip, Aix, _ = spmspm.dense_to_csr(A)
+    Bip, Bix, _ = spmspm.dense_to_csc(B)
+    cols = B.shape[1]
+    align, ks = set(), 0
+    for m in spmspm.alg1_matches(Aip, Aix, Bip, Bix, A.shape[0], cols):
+        sa, sb = m.a_pos % S, m.b_pos % S
+        if sa < sb:
+            align.add(("B", m.b_pos // S, sb - sa))
+        elif sb < sa:
+            align.add(("A", m.a_pos // S, sa - sb))
+        ks += len(ckks.rotation_plan((min(sa, sb) - (m.i * cols + m.j) % S) % S, S, base))
+    return ks + sum(len(ckks.rotation_plan(d, S, base)) for _, _, d in align)
+
+
+@pytest.mark.parametrize("seed,log_n,d,s", [(0, 6, 6, 0.5), (1, 7, 9, 0.3), (2, 12, 16, 0.75), (3, 16, 64, 0.9),
+                                          (4, 5, 6, 0.3)])
+def test_rotation_base_tuner_matches_oracle_counts(sp, seed, log_n, d, s):
+    """The host-only tuner picks, among the power-of-two bases whose keys fit
+    the budget, the one with the fewest key switches (ties: fewer keys), with
+    counts equal to the oracle planner's."""
+    from oracle import ckks
+    rng = np.random.default_rng(seed)
+    A = synthetic.bernoulli_sparse(rng, d, d, s)
+    B = synthetic.bernoulli_sparse(rng, d, d, s)
+    Aip, Aix, _ = spmspm.dense_to_csr(A)
+    Bip, Bix, _ = spmspm.dense_to_csc(B)
+    L, K, dnum = 5, 2, 2
+    S = 1 << (log_n - 1)
+    per_key = dnum * 2 * (L + K) * (1 << log_n) * 8
+    rows = []
+    b = 2
+    while b <= S:
+        rows.append((b, _plan_key_switches(A, B, S, b), len(ckks.rotation_key_amounts(S, b)) * per_key))
+        b *= 2
+    for budget in (max(r[2] for r in rows), sorted(r[2] for r in rows)[len(rows) // 2], min(r[2] for r in rows)):
+        fits = [r for r in rows if r[2] <= budget]
+        want = min(fits, key=lambda r: (r[1], r[2]))
+        got = sp.spfhe_tune_rotation_base(log_n, L, K, dnum, sp.sparse_meta(Aip, Aix, d, d),
+                                          sp.sparse_meta(Bip, Bix, d, d), budget)
+        assert got == want, (budget, got, want)
+    with pytest.raises(sp.SpfheError) as e:
+        sp.spfhe_tune_rotation_base(log_n, L, K, dnum, sp.sparse_meta(Aip, Aix, d, d),
+                                    sp.sparse_meta(Bip, Bix, d, d), min(r[2] for r in rows) - 1)
+    assert e.value.status == -2

@@ -1,5 +1,6 @@
-"""Pins for the oracle's key material: the switching-key formula of hybrid
-key switching and the three samplers.
+"""Pins for the oracle's key material and encryption: the switching-key
+formula of hybrid key switching, secret-key encryption, and the three
+samplers.
 
 Switching key from s' to s, digit j, over every modulus m of q_0..q_{L-1},
 p_0..p_{K-1}:  k_j = (-a_j s + e_j + g_j s', a_j) with g_j = P mod q_i on
@@ -145,3 +146,20 @@ def test_samplers():
     for i, m in enumerate(P.mods):
         assert int(u[i].max()) < m
         assert abs(float(np.mean(u[i].astype(np.float64))) / m - 0.5) < 5 * np.sqrt(1 / 12 / n)
+
+
+def test_encryption_formula(tiny):
+    """Secret-key encryption (c0, c1) = (-a s + e + m, a): c0 + c1 s - m is
+    one small integer error polynomial on every modulus of the level."""
+    P, o, keys = tiny
+    s = [int(v) for v in keys.s]
+    rng = np.random.default_rng(8)
+    pt = o.encode(rng.uniform(-1, 1, P.slots), P.L, P.scale)
+    ct = o.encrypt(pt, keys, rng)
+    errs = []
+    for i, m in enumerate(P.mods[: P.L]):
+        c1s = _negacyclic([int(v) for v in ct.c1[i]], s)
+        errs.append([_centred(int(ct.c0[i][t]) + c1s[t] - int(pt.m[i][t]), m) for t in range(P.n)])
+    for e in errs[1:]:
+        assert e == errs[0]
+    assert 0 < max(abs(v) for v in errs[0]) <= int(6 * SIGMA)

@@ -113,3 +113,23 @@ def test_rotation_base_tuner_matches_oracle_counts(sp, seed, log_n, d, s):
         sp.spfhe_tune_rotation_base(log_n, L, K, dnum, sp.sparse_meta(Aip, Aix, d, d),
                                     sp.sparse_meta(Bip, Bix, d, d), min(r[2] for r in rows) - 1)
     assert e.value.status == -2
+
+
+def test_no_cpu_fallback_without_a_gpu(sp):
+    """On a host without a usable GPU the library computes nothing: creating
+    a context fails with SPFHE_ECUDA and a message, and calls given no context
+    fail with SPFHE_EINVAL.  (On a GPU host this test has nothing to check.)"""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2604_11659_gb300 import params as gparams
+    with pytest.raises(sp.SpfheError) as e:
+        sp.spfhe_ctx_create(gparams.ctx_params(synthetic.ring_tiny()))
+    assert e.value.status == -6 and str(e.value)
+    lib = sp.lib()
+    n = ctypes.c_size_t(0)
+    assert lib.spfhe_keys_export(None, None, None, None, ctypes.byref(n), None, None) == -1
+    assert lib.spfhe_prof_alu_peak(None, None, None, None, None) == -1
+    assert lib.spfhe_rescale_noalloc(None, None, 2, None) == -1
+    assert lib.spfhe_sync(None) == -1

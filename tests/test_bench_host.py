@@ -59,3 +59,23 @@ def test_check_reports_max_abs_and_frobenius_errors():
     g.case = types.SimpleNamespace(A=A, B=B)
     assert abs(g.check(["chunk"]) - 4e-7) < 1e-15
     assert abs(g.last_frobenius - 5e-7) < 1e-15
+
+
+def test_clock_summary_parses_samples_and_reasons(tmp_path):
+    """The nvidia-smi samples taken during the timed region: median SM clock,
+    the maximum, and every throttle reason seen Active."""
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1980, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbage line\n")
+    c = bench.ClockSampler(0)
+    c.path = str(path)
+    out = c.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not path.exists()
+    empty = tmp_path / "empty.csv"
+    empty.write_text("")
+    c.path = str(empty)
+    assert c.summary()["reasons"] == ["no samples"]

@@ -695,6 +695,8 @@ def main():
     ap.add_argument("--workload", default="128x128", choices=["128x128", "16x16"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--rot-base", type=int, default=256)
+    ap.add_argument("--key-budget-gb", type=float, default=40.0,
+                    help="rotation-key memory budget under which the rotation-base tuner's pick is reported")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-products", type=int, default=16)
@@ -863,6 +865,16 @@ def main():
                    "ks_relin": st_g["ks_relin"], "ks_align": st_g["ks_align"], "ks_final": st_g["ks_final"],
                    "speedup_vs_alg2": ms_step / ms_g}
 
+    # the rotation-plan base the host-only tuner picks for this product under
+    # the key budget, beside the base the step ran with
+    try:
+        rb_pick, rb_ks, rb_bytes = sp.spfhe_tune_rotation_base(g.rec.log_n, Lr, g.K, g.rec.dnum, g.Am, g.Bm,
+                                                               int(args.key_budget_gb * (1 << 30)))
+        rot_base_info = {"used": args.rot_base, "tuner_pick": rb_pick, "key_budget_gib": args.key_budget_gb,
+                         "tuner_rotation_key_switches": rb_ks, "tuner_key_gib": rb_bytes / (1 << 30)}
+    except sp.SpfheError as exc:
+        rot_base_info = {"used": args.rot_base, "tuner_error": str(exc)}
+
     hbm_peak, sm_max, peak_src = load_peaks()
     kernels = {}
     for name, d in prof.items():
@@ -906,7 +918,8 @@ def main():
                        "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},
             "e2e": {"value": e2e_val, "unit": "matmuls/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
-            "max_abs_err": err, "frobenius_err": frob, "keygen_s": round(g.keygen_s, 2), "graph": graph,
+            "max_abs_err": err, "frobenius_err": frob, "rotation_base": rot_base_info,
+            "keygen_s": round(g.keygen_s, 2), "graph": graph,
             "variant_grouped": variant,
             "keyswitch": {"polys": ks_calls, "gbs": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9,
                           "frac_of_hbm": ks_bytes / max(1e-12, ks_ms * 1e-3) / 1e9 / hbm_peak},

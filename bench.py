@@ -743,7 +743,7 @@ def main():
     gbuild.build()
     stream = torch.cuda.current_stream().cuda_stream
     case = make_workload(args.workload, rank_seed(args.seed, rank))
-    g = GpuMatmul(case, args.rot_base, stream, ntt_chunk=args.ntt_chunk)
+    g = GpuMatmul(case, args.rot_base, stream, ntt_chunk=args.ntt_chunk, ntt_variant=args.ntt_variant)
     sp = g.sp
 
     for _ in range(max(3, args.warmup)):

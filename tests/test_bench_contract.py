@@ -1,0 +1,175 @@
+"""bench.py's main path on CPU: the library, the workload object and CUDA
+timing are replaced by stubs with fixed timings, so the glue that turns
+measurements into the one JSON line (keys, units, the whole-job rate, the
+roofline, the end-to-end copies, the optional sub-measurements) runs without
+a GPU and is checked against the numbers the stubs produced."""
+import json
+import sys
+import types
+
+import numpy as np
+import pytest
+
+import bench
+
+CLASSES = ["ntt_fwd", "ntt_inv", "modup_bconv", "ks_inner_product", "moddown_bconv", "moddown_final", "tensor",
+           "rescale", "automorph", "mask_mul", "accumulate", "other", "ks_ntt_fwd", "ks_ntt_inv"]
+STEP_MS = 2000.0
+
+
+class FakeEvent:
+    clock = 0.0
+
+    def __init__(self, enable_timing=True):
+        self.t = 0.0
+
+    def record(self):
+        FakeEvent.clock += STEP_MS
+        self.t = FakeEvent.clock
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class SpfheError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(msg)
+        self.status = status
+
+
+def fake_library():
+    sp = types.SimpleNamespace()
+    sp.SpfheError = SpfheError
+    sp.launches = 0
+    sp.spfhe_prof_alu_peak = lambda ctx: (1.1e12, 1.2e12, 2.0e13, 7.2e12)
+    sp.spfhe_prof_enable = lambda ctx, on: None
+    sp.spfhe_launch_count = lambda ctx: sp.launches
+
+    def prof_all(ctx):
+        d = {c: {"launches": 0, "ms": 0.0, "bytes": 0.0, "work": 0.0} for c in CLASSES}
+        d["ks_ntt_fwd"] = {"launches": 100, "ms": 600.0, "bytes": 2.0e12, "work": 4.0e11}
+        d["modup_bconv"] = {"launches": 50, "ms": 200.0, "bytes": 3.0e11, "work": 1.0e11}
+        d["ks_inner_product"] = {"launches": 50, "ms": 100.0, "bytes": 5.0e11, "work": 0.0}
+        return d
+    sp.spfhe_prof_all = prof_all
+    sp.spfhe_prof_keyswitch = lambda ctx: (1000, 7.5e10)
+    sp.spfhe_ct_export = lambda ctx, h, n, out=None: out
+    sp.spfhe_ct_import = lambda ctx, ptr, level, scale: ("ct", ptr)
+    sp.matmul_req = lambda *a: a
+    sp.spfhe_matmul_graph_create = lambda ctx, req, variant: "graph"
+    sp.spfhe_matmul_graph_launch = lambda gr: None
+    sp.spfhe_matmul_graph_results = lambda gr, n_c: (["c"] * n_c, {"launches": 40180})
+    sp.spfhe_ct_free = lambda h: None
+    sp.spfhe_matmul_graph_free = lambda gr: None
+    sp.spfhe_tune_rotation_base = lambda *a: (256, 48014, 37251710976)
+    sp.spfhe_keys_free = lambda k: None
+    sp.spfhe_ctx_destroy = lambda ctx: None
+    return sp
+
+
+class FakeMatmul:
+    def __init__(self, case, rot_base, stream, ntt_chunk=-1, ntt_variant=0):
+        self.sp = SP
+        self.case = case
+        self.rec = case.ring
+        self.ctx, self.keys = "ctx", "keys"
+        self.K = 7
+        self.n = 1 << 6                   # small buffers for the host copies
+        self.n_c = 1
+        self.A_cts, self.B_cts = ["a0"], ["b0"]
+        self.Am = self.Bm = None
+        self.rows, self.inner, self.cols = case.A.shape[0], case.A.shape[1], case.B.shape[1]
+        self.nnz = (np.count_nonzero(case.A), np.count_nonzero(case.B))
+        self.ntt_chunk, self.ntt_tune = (4, 8, 0), None
+        self.keygen_s = 1.0
+        self.last_frobenius = 0.0
+
+    def step(self, A_cts=None, B_cts=None, grouped=False):
+        SP.launches += 40180
+        st = {"matches": 21310, "ks_relin": 21310, "ks_align": 5483, "ks_final": 42531, "rescales": 42620}
+        if grouped:
+            st = {"matches": 21310, "ks_relin": 11403, "ks_align": 3003, "ks_final": 11423, "rescales": 22806}
+        return ["c"], st
+
+    def free(self, outs):
+        pass
+
+    def check(self, outs):
+        self.last_frobenius = 5e-6
+        return 4e-7
+
+
+SP = fake_library()
+
+
+@pytest.fixture
+def stubbed(monkeypatch):
+    torch = pytest.importorskip("torch")
+    FakeEvent.clock = 0.0
+    SP.launches = 0
+    monkeypatch.setattr(torch.cuda, "set_device", lambda i: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda.profiler, "start", lambda: None)
+    monkeypatch.setattr(torch.cuda.profiler, "stop", lambda: None)
+    from paper_2604_11659_gb300 import build as gbuild
+    monkeypatch.setattr(gbuild, "build", lambda *a, **k: None)
+    monkeypatch.setattr(bench, "GpuMatmul", FakeMatmul)
+    monkeypatch.setattr(bench, "_pinned", lambda shape: np.zeros(shape, np.uint64))
+    monkeypatch.setattr(bench, "batch_vs_plain", lambda *a, **k: {"speedup": 1.7})
+    monkeypatch.setattr(bench, "serve_run", lambda *a, **k: {"served": {"p99_ms": 1.0}})
+    monkeypatch.setattr(bench, "dense_layer_pt", lambda *a, **k: {"ms": 1.0})
+    monkeypatch.setattr(bench, "cpu_baseline_line", lambda *a, **k: {"value": 2e-5, "unit": "matmuls/s",
+                                                                      "cores": 8, "kind": "oracle", "sample": "s"})
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+
+
+def _run(monkeypatch, capsys, argv):
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    bench.main()
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_default_line_carries_the_contract(stubbed, monkeypatch, capsys):
+    line = _run(monkeypatch, capsys, ["--steps", "2", "--warmup", "3"])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks", "roofline",
+              "cpu_baseline"):
+        assert k in line, k
+    assert line["n_gpus"] == 1 and line["steps"] == 2 and line["warmup"] == 3 and line["scaling"] == "weak"
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None and line["dtype"] == "u64"
+    # two timed steps between two event records: the stub clock advanced by one STEP_MS
+    assert line["ms_per_step"] == pytest.approx(STEP_MS / 2)
+    assert line["value"] == pytest.approx(2 / (STEP_MS / 1e3))
+    assert line["gpu_launches"] == 2 * 40180
+    assert line["config"]["workload"].startswith("128x128 ct x ct")
+    e2e = line["e2e"]
+    assert e2e["h2d_bytes_per_step"] == 2 * 2 * 24 * 64 * 8 and e2e["d2h_bytes_per_step"] == 2 * 22 * 64 * 8
+    roof = line["roofline"]
+    assert roof["kernel"] == "ks_ntt_fwd" and roof["bound"] == "alu"
+    assert roof["achieved"] == pytest.approx(4.0e11 / 0.6 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["traffic"] is None and "variant 4" in roof["traffic_source"]
+    assert roof["alu_microbench"]["frac_of_butterfly_peak"] == pytest.approx(4.0e11 / 0.6 / 1.2e12)
+    assert line["max_abs_err"] == 4e-7 and line["frobenius_err"] == 5e-6
+    assert line["rotation_base"] == {"used": 256, "tuner_pick": 256, "key_budget_gib": 40.0,
+                                     "tuner_rotation_key_switches": 48014,
+                                     "tuner_key_gib": pytest.approx(37251710976 / 2 ** 30)}
+    assert line["graph"]["vs_eager"] == pytest.approx(1.0)
+    assert line["variant_grouped"]["ks_per_step"] == 11403 + 3003 + 11423
+    for k in ("batch", "serve", "dense_layer_ct_pt"):
+        assert k in line
+
+
+def test_skips_leave_their_keys_out(stubbed, monkeypatch, capsys):
+    line = _run(monkeypatch, capsys, ["--steps", "1", "--warmup", "3", "--graph-steps", "0", "--grouped-steps", "0",
+                                      "--batch-products", "0", "--serve-requests", "0", "--dense-layer", "0",
+                                      "--no-cpu-baseline"])
+    assert line["graph"] is None and line["variant_grouped"] is None
+    for k in ("batch", "serve", "dense_layer_ct_pt", "cpu_baseline"):
+        assert k not in line
+    assert line["ms_per_step"] == pytest.approx(STEP_MS)

@@ -188,6 +188,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+def workload_desc(name: str, case, K: int, rot_base: int) -> str:
+    """The workload named in both arms' config: product, sparsity of A, ring."""
+    A, rec = case.A, case.ring
+    sparsity = round(100 * (1 - np.count_nonzero(A) / A.size))
+    return "%s ct x ct, %d%% sparsity, N=2^%d, L=%d, dnum=%d, K=%d, rot_base=%d" % (
+        name, sparsity, rec.log_n, rec.L, rec.dnum, K, rot_base)
+
+
 def make_workload(name: str, seed: int):
     from paper_2604_11659_gb300 import synthetic
     if name == "128x128":
@@ -616,10 +624,10 @@ def cpu_baseline_line(case, rot_base):
     cpu_s, proj = s.run()
     return {"value": 1.0 / proj, "unit": "matmuls/s", "cores": cores, "kind": "oracle",
             "sample": ("one tensor + relinearisation + 2 rescales + mask product + key switch at level L-2 + add "
-                       "at N=2^16, L=24, dnum=3 (%.1f s wall on the host cores, limb loops on OpenMP threads), "
+                       "at N=2^%d, L=%d, dnum=%d (%.1f s wall on the host cores, limb loops on OpenMP threads), "
                        "projected with the workload's exact counts: "
                        "%d matches, %d final-rotation and %d alignment key switches"
-                       % (cpu_s, s.matches, s.ks_final, s.ks_align))}
+                       % (case.ring.log_n, case.ring.L, case.ring.dnum, cpu_s, s.matches, s.ks_final, s.ks_align))}
 
 
 # ---------------------------------------------------------------------------
@@ -644,8 +652,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": val, "unit": "matmuls/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "128x128 ct x ct, 90% sparsity, N=2^16, L=24, dnum=3, K=7, rot_base=%d"
-                       % args.rot_base, "l2": "working set >> L2"},
+            "config": {"workload": workload_desc(args.workload, case, s.P.K, args.rot_base),
+                       "l2": "working set >> L2"},
             "cpu_baseline": {"value": val, "unit": "matmuls/s", "cores": cores, "kind": "oracle",
                              "sample": "per step: one sample of the per-match ops (%.1f s CPU), projected with "
                                        "exact op counts (%d matches)" % (cpu_total / args.steps, s.matches)},
@@ -910,9 +918,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "matmuls/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "%s ct x ct, %d%% sparsity, N=2^%d, L=%d, dnum=%d, K=%d, rot_base=%d"
-                       % (args.workload, round(100 * (1 - g.nnz[0] / (g.rows * g.inner))), g.rec.log_n, Lr,
-                          g.rec.dnum, g.K, args.rot_base),
+            "config": {"workload": workload_desc(args.workload, case, g.K, args.rot_base),
                        "matches": st["matches"], "ks_per_step": st["ks_relin"] + st["ks_align"] + st["ks_final"],
                        "ntt_variant_split_chunk": list(g.ntt_chunk), "ntt_tuning_ms": g.ntt_tune,
                        "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},

@@ -173,3 +173,19 @@ def test_skips_leave_their_keys_out(stubbed, monkeypatch, capsys):
     for k in ("batch", "serve", "dense_layer_ct_pt", "cpu_baseline"):
         assert k not in line
     assert line["ms_per_step"] == pytest.approx(STEP_MS)
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """--impl reference times the oracle (here on the small 16x16 workload so
+    the test stays short) and prints the same metric and config as the
+    library's arm, with impl, cpu_baseline and a zero-copy e2e."""
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    line = _run(monkeypatch, capsys, ["--impl", "reference", "--workload", "16x16", "--steps", "1", "--warmup", "0"])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "matmuls/s"
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["config"]["workload"].startswith("16x16 ct x ct, ") and "N=2^12, L=4" in line["config"]["workload"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "matmuls/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

@@ -738,10 +738,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
+    # one rank per GPU over NCCL; gloo on a host without CUDA (the CPU tests
+    # of this path run the ranks as processes with a stub library)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = "cuda"
+        dist.init_process_group("nccl" if dev == "cuda" else "gloo")
 
     def barrier():
         if dist is not None:

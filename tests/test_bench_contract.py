@@ -189,3 +189,66 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "matmuls/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def _install_stubs(rank):
+    """The fixture's stubs, installed directly in a spawned rank process; the
+    rank's device clock runs (rank + 1) times slower."""
+    import torch
+    from paper_2604_11659_gb300 import build as gbuild
+
+    class RankEvent(FakeEvent):
+        def record(self):
+            FakeEvent.clock += STEP_MS * (rank + 1)
+            self.t = FakeEvent.clock
+
+    torch.cuda.set_device = lambda i: None
+    torch.cuda.synchronize = lambda *a: None
+    torch.cuda.current_stream = lambda *a: types.SimpleNamespace(cuda_stream=0)
+    torch.cuda.Event = RankEvent
+    torch.cuda.profiler.start = lambda: None
+    torch.cuda.profiler.stop = lambda: None
+    gbuild.build = lambda *a, **k: None
+    bench.GpuMatmul = FakeMatmul
+    bench._pinned = lambda shape: np.zeros(shape, np.uint64)
+    bench.batch_vs_plain = lambda *a, **k: {"speedup": 1.7}
+    bench.serve_run = lambda *a, **k: {"served": {"p99_ms": 1.0}}
+    bench.dense_layer_pt = lambda *a, **k: {"ms": 1.0}
+
+
+def _bench_rank(rank, world, port, out_dir):
+    import os
+    os.environ.update({"WORLD_SIZE": str(world), "RANK": str(rank), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    _install_stubs(rank)
+    sys.argv = ["bench.py", "--gpus", str(world), "--steps", "2", "--warmup", "3"]
+    with open(os.path.join(out_dir, "rank%d.out" % rank), "w") as f:
+        old = sys.stdout
+        sys.stdout = f
+        try:
+            bench.main()
+        finally:
+            sys.stdout = old
+
+
+def test_two_ranks_print_one_line_with_the_slowest_time(tmp_path):
+    """bench.py under two ranks (gloo, processes): rank 0 alone prints, the
+    time is the slowest rank's, and the value counts both ranks' products."""
+    import socket
+
+    import torch.multiprocessing as mp
+    pytest.importorskip("torch")
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_bench_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    out0 = [ln for ln in (tmp_path / "rank0.out").read_text().splitlines() if ln.strip()]
+    assert (tmp_path / "rank1.out").read_text().strip() == ""
+    assert len(out0) == 1
+    line = json.loads(out0[0])
+    # rank 1's clock is twice as slow: two steps took 2 * STEP_MS there
+    assert line["n_gpus"] == 2 and line["scaling"] == "weak"
+    assert line["ms_per_step"] == pytest.approx(2 * STEP_MS / 2)
+    assert line["value"] == pytest.approx(2 * 2 / (2 * STEP_MS / 1e3))
+    assert "cpu_baseline" not in line
+    assert line["variant_grouped"]["ms_per_step"] == pytest.approx(2 * STEP_MS / 2)

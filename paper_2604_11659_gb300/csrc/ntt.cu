@@ -12,6 +12,8 @@
 //     takes 16 adjacent columns so every row read is a 128-byte segment;
 //   pass B covers stages [PA, log_n): contiguous tiles of 2^(log_n-PA).
 // Residues are kept fully reduced in [0, q) between stages.
+#include <atomic>
+
 #include "kernels.h"
 
 namespace spfhe {
@@ -684,8 +686,10 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
         p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = mul_shoup(v[i], m.n_inv, m.n_inv_p, q);
 }
 
-// dynamic shared memory of pass B for variant V (opted in once per kernel;
-// DIR tells the forward and inverse kernels apart, their types are equal)
+// dynamic shared memory of pass B for variant V (opted in once per kernel and
+// device: the attribute belongs to the kernel's instance on the current
+// device; DIR tells the forward and inverse kernels apart, their types are
+// equal)
 template <int P, int V, int DIR, typename K> size_t r16_b_smem(K kernel)
 {
     if constexpr (V != 2) {
@@ -693,10 +697,13 @@ template <int P, int V, int DIR, typename K> size_t r16_b_smem(K kernel)
         return 0;
     } else {
         const size_t bytes = (size_t)r16_tw_smem_entries<P>() * sizeof(ulonglong2);
-        static bool done = false;
-        if (!done) {
+        static std::atomic<uint64_t> done{0};   // bit d: set on device d (d < 64)
+        int dev = 0;
+        SPFHE_CHECK_CUDA(cudaGetDevice(&dev));
+        const uint64_t bit = dev < 64 ? 1ull << dev : 0;
+        if (!bit || !(done.load() & bit)) {
             SPFHE_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-            done = true;
+            done.fetch_or(bit);
         }
         return bytes;
     }

@@ -133,3 +133,46 @@ def test_no_cpu_fallback_without_a_gpu(sp):
     assert lib.spfhe_prof_alu_peak(None, None, None, None, None) == -1
     assert lib.spfhe_rescale_noalloc(None, None, 2, None) == -1
     assert lib.spfhe_sync(None) == -1
+
+
+def test_planner_fuzz_valid_or_refused(sp):
+    """Random shapes and densities, some with one corrupted index or pointer
+    (or mismatched inner dimensions): the host planner either returns the
+    oracle's matches or refuses the metadata with SPFHE_EINVAL."""
+    rng = np.random.default_rng(123)
+    planned = refused = 0
+    for _ in range(600):
+        rows, inner, cols = (int(x) for x in rng.integers(1, 10, 3))
+        A = (rng.random((rows, inner)) < rng.random()) * 1.0
+        B = (rng.random((inner, cols)) < rng.random()) * 1.0
+        Aip, Aix, _ = spmspm.dense_to_csr(A)
+        Bip, Bix, _ = spmspm.dense_to_csc(B)
+        Aip, Aix, Bip, Bix = (np.array(x, np.int32) for x in (Aip, Aix, Bip, Bix))
+        mode = int(rng.integers(0, 5))
+        b_inner = inner
+        if mode == 1 and Aix.size:
+            Aix[rng.integers(0, Aix.size)] = rng.integers(-3, inner + 3)
+        elif mode == 2:
+            Aip[rng.integers(1, Aip.size)] = rng.integers(0, max(1, Aix.size))
+        elif mode == 3 and Bix.size:
+            Bix[rng.integers(0, Bix.size)] = rng.integers(-3, inner + 3)
+        elif mode == 4:
+            b_inner = inner + 1
+        Am = sp.sparse_meta(Aip, Aix, rows, inner)
+        Bm = sp.sparse_meta(Bip, Bix, b_inner, cols)
+        if Am.nnz > Aix.size:      # a pointer past the caller's index array: not the library's to detect
+            continue
+        valid = (np.all(np.diff(Aip) >= 0) and all(np.all(np.diff(Aix[Aip[i]:Aip[i + 1]]) > 0) for i in range(rows))
+                 and np.all((Aix >= 0) & (Aix < inner)) and np.all((Bix >= 0) & (Bix < inner))
+                 and all(np.all(np.diff(Bix[Bip[j]:Bip[j + 1]]) > 0) for j in range(cols)) and b_inner == inner)
+        try:
+            got = sp.spfhe_plan_matches(Am, Bm)
+        except sp.SpfheError as e:
+            assert e.status == -1 and not valid
+            refused += 1
+            continue
+        assert valid
+        want = [(m.i, m.j, m.k, m.a_pos, m.b_pos) for m in spmspm.alg1_matches(Aip, Aix, Bip, Bix, rows, cols)]
+        assert [tuple(int(v) for v in r) for r in got] == want
+        planned += 1
+    assert planned > 200 and refused > 50

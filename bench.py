@@ -108,6 +108,8 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 
 
 NTT_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv"}
+# the kernel classes of key switching (for the key switch's GB/s)
+KS_CLASSES = ("modup_bconv", "ks_inner_product", "moddown_bconv", "moddown_final", "ks_ntt_fwd", "ks_ntt_inv")
 
 
 def alu_microbench(meas, achieved_bfly, sm_mhz, sms=152):
@@ -913,8 +915,7 @@ def main():
         achieved = dd["bytes"] / (dd["ms"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src}
-    ks_cls = ["modup_bconv", "ks_inner_product", "moddown_bconv", "moddown_final", "ks_ntt_fwd", "ks_ntt_inv"]
-    ks_ms = sum(prof[c]["ms"] for c in ks_cls)
+    ks_ms = sum(prof[c]["ms"] for c in KS_CLASSES)
     ks_calls, ks_bytes = ks_info
 
     line = {"metric": METRIC, "value": value, "unit": "matmuls/s", "n_gpus": world, "steps": args.steps,

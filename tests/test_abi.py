@@ -176,3 +176,11 @@ def test_planner_fuzz_valid_or_refused(sp):
         assert [tuple(int(v) for v in r) for r in got] == want
         planned += 1
     assert planned > 200 and refused > 50
+
+
+def test_bench_kernel_classes_exist_in_the_library(sp):
+    """Every kernel class bench.py reads from the profiler is one the library
+    reports (a renamed class would otherwise fail only on the GPU)."""
+    import bench
+    names = {sp.spfhe_prof_class_name(c) for c in range(sp.spfhe_prof_classes())}
+    assert bench.ALU_CLASSES <= names and bench.NTT_CLASSES <= names and set(bench.KS_CLASSES) <= names

@@ -32,8 +32,8 @@ ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", 
 
 # DRAM bytes (read + write) per limb of each forward-transform pass kind, from
 # ncu captures of the radix-16 kernels (4 CTAs per SM, split 8/8) on the
-# profiler case (bench.py --small-case --ntt-variant 3: n = 2^16, 288-345 limbs
-# per launch): pass A, pass B, and pass B with the fused ModDown epilogue.
+# profiler case (bench.py --small-case: n = 2^16): pass A, pass B, and pass B
+# with the fused ModDown epilogue.
 NTT_FWD_DRAM_PER_LIMB = {"a": (151.2e6 + 90.8e6) / 288, "b": (250.2e6 + 138.6e6) / 345,
                          "b_moddown": (456.6e6 + 150.7e6) / 288}
 
@@ -51,21 +51,23 @@ def traffic_source(dom, variant):
     return "ncu DRAM bytes per limb of the profiler case, scaled to the launch's limbs by pass kind"
 
 
-def ks_ntt_fwd_traffic(work, nbytes, launches, n, log_n):
-    """DRAM bytes per launch of the key-switching forward transforms.  The
-    class's limbs are split by pass kind from its totals: every limb costs
-    (n/2)·log2(n) butterflies over its two passes, and every pass-B launch
-    pairs with a pass-A launch, so pass-A limbs LA = work / ((n/2)·log2 n);
-    algorithmic bytes are 16n per limb of pass A or plain pass B and 40n per
-    limb of the fused ModDown pass B, so fused limbs LF = (bytes - 32n·LA) /
-    24n and plain pass-B limbs LB = LA - LF.  Assumes DRAM bytes grow in
-    proportion to the limbs (the profiler case and the bench both stream
-    limbs far larger than L2 with the same per-limb access pattern)."""
-    la = work / (0.5 * n * log_n)
-    lf = min(la, max(0.0, (nbytes - 32.0 * n * la) / (24.0 * n)))
-    lb = la - lf
+def ks_ntt_fwd_traffic(limbs, launches):
+    """DRAM bytes per launch of the key-switching forward transforms: the
+    limbs the class transformed by pass kind (first pass, plain second pass,
+    second pass with the fused ModDown epilogue; counted by the library) times
+    each kind's DRAM bytes per limb from the ncu captures.  Assumes DRAM bytes
+    grow in proportion to the limbs (the profiler case and the bench both
+    stream limbs far larger than L2 with the same per-limb access pattern)."""
+    la, lb, lf = limbs
     d = NTT_FWD_DRAM_PER_LIMB
     return (la * d["a"] + lb * d["b"] + lf * d["b_moddown"]) / max(1, launches)
+
+
+def bench_config(workload: str) -> dict:
+    """The `config` of both arms' lines: the workload and nothing that
+    depends on the implementation."""
+    return {"workload": workload, "l2": "inputs+keys >> 129 MB L2 (no flush)",
+            "parallelism": "independent products per GPU"}
 
 
 def load_peaks():
@@ -115,20 +117,22 @@ KS_CLASSES = ("modup_bconv", "ks_inner_product", "moddown_bconv", "moddown_final
 def alu_microbench(meas, achieved_bfly, sm_mhz, sms=152):
     """The library's measured ALU speed of light beside the derived peak:
     butterflies/s of register-resident lazy forward butterflies (the
-    transforms' own Shoup arithmetic, no memory traffic; as 64-bit-result
-    multiplies and as split halves), and the 32-bit multiply-add rates per
-    SM per clock that calibrate the derivation.  The fraction is taken
-    against the faster butterfly form."""
+    transforms' own Shoup arithmetic, no memory traffic: wide products, split
+    halves, and the shorter quotient), and the 32-bit multiply-add rates per
+    SM per clock that calibrate the derivation (low half, 64-bit result, high
+    half).  The fraction is taken against the fastest butterfly form."""
     if meas is None:
         return None
-    bfly, bfly_split, imad, wide = meas
+    bfly, bfly_split, bfly_short, imad, wide, hi = meas
     clk = sms * sm_mhz * 1e6
     out = {"butterflies_per_s": bfly, "butterflies_split_per_s": bfly_split,
-           "imad_per_s": imad, "imad_wide_per_s": wide,
+           "butterflies_short_quotient_per_s": bfly_short,
+           "imad_per_s": imad, "imad_wide_per_s": wide, "imad_hi_per_s": hi,
            "imad_per_clk_per_sm": imad / clk, "imad_wide_per_clk_per_sm": wide / clk,
-           "what": "register-resident microbenchmarks at 4 CTAs x 256 threads per SM (spfhe_prof_alu_peak)"}
+           "imad_hi_per_clk_per_sm": hi / clk,
+           "what": "register-resident microbenchmarks at 4 CTAs x 256 threads per SM (spfhe_prof_alu_rates)"}
     if achieved_bfly is not None:
-        out["frac_of_butterfly_peak"] = achieved_bfly / max(bfly, bfly_split)
+        out["frac_of_butterfly_peak"] = achieved_bfly / max(bfly, bfly_split, bfly_short)
     return out
 
 
@@ -232,7 +236,7 @@ def tune_ntt(sp, ctx, rec, chunk, variant=0):
     items = 32 if rec.log_n >= 15 else 64
     splits = [pa for pa in range(6, 10) if 6 <= rec.log_n - pa <= 9] if rec.log_n >= 12 else [0]
     best, timings = None, {}
-    for var in (0, 1, 2, 3, 4):
+    for var in (0, 1, 2, 3, 4, 5):
         sp.spfhe_ctx_set_ntt_variant(ctx, var)
         for pa in splits:
             sp.spfhe_ctx_set_ntt_split(ctx, pa)
@@ -348,20 +352,42 @@ def _encrypt_case(sp, ctx, keys, case, level, scale, seed):
     return Am, enc(Ad, seed), Bm, enc(Bd, seed + 500), max(1, -(-(case.A.shape[0] * case.B.shape[1]) // S))
 
 
-def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
+def decrypt_matrix(sp, ctx, keys, handles, rows, cols, S):
+    """Decrypt and decode a product's result chunks into a rows x cols matrix."""
+    vals = []
+    for h in handles:
+        pt = sp.spfhe_decrypt(ctx, keys, h)
+        vals.append(sp.spfhe_decode(ctx, pt, S).real)
+        sp.spfhe_pt_free(pt)
+    return np.concatenate(vals)[: rows * cols].reshape(rows, cols)
+
+
+def product_errors(errs):
+    """Worst max-abs and Frobenius error over a list of (max_abs, frobenius)."""
+    if not errs:
+        return {"max_abs_err": None, "frobenius_err": None, "checked": 0}
+    return {"max_abs_err": max(e[0] for e in errs), "frobenius_err": max(e[1] for e in errs), "checked": len(errs)}
+
+
+def batch_vs_plain(stream, count, dims, seed=2, ntt=(5, 0, 0), sparsity=(0.70, 0.95), op_by_op=True, warmup=True):
     """`count` products of the batch workload's recipe (d from `dims`,
-    sparsity U[0.70, 0.95], half Bernoulli / half 2:4) on its ring (N=2^16,
-    L=20, dnum=4): one spfhe_sparse_matmul_batch call against one
-    spfhe_sparse_matmul_ct_ct call per product.  Both produce identical bits."""
+    sparsity uniform in `sparsity`, half Bernoulli / half 2:4) on its ring
+    (N=2^16, L=20, dnum=4): one spfhe_sparse_matmul_batch call, and the same
+    batch captured once as a CUDA graph, against the plain path (one
+    spfhe_sparse_matmul_ct_ct call per product) and optionally Alg. 2 op by
+    op (one match per launch sequence).  Every product of the batched call is
+    decrypted and compared with FP64, and its chunks are compared bit for
+    bit with the plain path's."""
     import torch
     from paper_2604_11659_gb300 import params as gparams
     from paper_2604_11659_gb300 import spfhe as sp
     from paper_2604_11659_gb300 import synthetic
-    cases = synthetic.batch64_cases(seed=seed, count=count, dims=dims)
+    cases = synthetic.batch64_cases(seed=seed, count=count, dims=dims, sparsity=sparsity)
     rec = cases[0].ring
     ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
     set_ntt(sp, ctx, ntt)
     keys = sp.spfhe_keygen(ctx, 99)
+    S = (1 << rec.log_n) // 2
     prods = [_encrypt_case(sp, ctx, keys, c, rec.L, rec.scale, 10 * i) for i, c in enumerate(cases)]
     reqs = [sp.matmul_req(keys, Am, a, Bm, b) for Am, a, Bm, b, _ in prods]
     ncs = [p[4] for p in prods]
@@ -392,13 +418,16 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
         sp.spfhe_matmul_graph_launch(graph)
         return [], None
 
-    res = {}
-    for name, fn in (("plain", per_product(1)), ("per_product", per_product(0)), ("batched", batched),
-                     ("graph", graphed)):
-        outs, _ = fn()   # warm-up
-        for o in outs:
-            for h in o:
-                sp.spfhe_ct_free(h)
+    arms = [("plain", per_product(0)), ("batched", batched), ("graph", graphed)]
+    if op_by_op:
+        arms.insert(0, ("op_by_op", per_product(1)))
+    res, kept, m = {}, {}, 0
+    for name, fn in arms:
+        if warmup:
+            outs, _ = fn()
+            for o in outs:
+                for h in o:
+                    sp.spfhe_ct_free(h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         outs, mm = fn()
@@ -406,12 +435,32 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
         res[name] = time.perf_counter() - t0
         if mm is not None:
             m = mm
-        for o in outs:
+        if name in ("plain", "batched"):
+            kept[name] = outs
+        else:
+            for o in outs:
+                for h in o:
+                    sp.spfhe_ct_free(h)
+    # correctness: every batched product against FP64 and bit for bit against the plain path
+    errs, same = [], True
+    for c, ob, op in zip(cases, kept["batched"], kept["plain"]):
+        C = decrypt_matrix(sp, ctx, keys, ob, c.A.shape[0], c.B.shape[1], S)
+        D = C - c.A @ c.B
+        errs.append((float(np.max(np.abs(D))), float(np.sqrt(np.sum(D * D)))))
+        for hb, hp in zip(ob, op):
+            same = same and np.array_equal(sp.spfhe_ct_export(ctx, hb, 1 << rec.log_n),
+                                           sp.spfhe_ct_export(ctx, hp, 1 << rec.log_n))
+    for k in kept.values():
+        for o in k:
             for h in o:
                 sp.spfhe_ct_free(h)
     sp.spfhe_sync(ctx)
     g_outs, g_st = sp.spfhe_matmul_graph_results_batch(graph, ncs)
-    for o in g_outs:
+    g_errs = []
+    for c, o in zip(cases, g_outs):
+        C = decrypt_matrix(sp, ctx, keys, o, c.A.shape[0], c.B.shape[1], S)
+        D = C - c.A @ c.B
+        g_errs.append((float(np.max(np.abs(D))), float(np.sqrt(np.sum(D * D)))))
         for h in o:
             sp.spfhe_ct_free(h)   # handles only: the chunks belong to the graph
     sp.spfhe_matmul_graph_free(graph)
@@ -420,17 +469,22 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(0, 0, 0)):
             sp.spfhe_ct_free(h)
     sp.spfhe_keys_free(keys)
     sp.spfhe_ctx_destroy(ctx)
-    return {"workload": "%d products, d in %s, sparsity U[0.70,0.95] half 2:4, N=2^16, L=20, dnum=4 (scaled from "
-                        "64 products of d in {32..256})" % (count, list(dims)),
-            "plain": "one product per call, one match per launch sequence (Alg. 2 op by op)",
-            "matches": m, "plain_s": res["plain"], "per_product_batched_s": res["per_product"],
-            "batched_s": res["batched"],
-            "products_per_s_plain": count / res["plain"], "products_per_s_batched": count / res["batched"],
-            "speedup": res["plain"] / res["batched"],
-            "speedup_over_per_product_batching": res["per_product"] / res["batched"],
-            "graph_s": res["graph"], "graph_capture_s": round(capture_s, 2),
-            "graph_kernels": int(g_st[0]["launches"]),
-            "products_per_s_graph": count / res["graph"]}
+    out = {"workload": "%d products, d in %s, sparsity U[%.2f,%.2f] half 2:4, N=2^16, L=20, dnum=4"
+                       % (count, list(dims), sparsity[0], sparsity[1]),
+           "plain": "one spfhe_sparse_matmul_ct_ct call per product (matches of a product batched in its launches)",
+           "matches": m, "plain_s": res["plain"], "batched_s": res["batched"], "graph_s": res["graph"],
+           "products_per_s_plain": count / res["plain"], "products_per_s_batched": count / res["batched"],
+           "products_per_s_graph": count / res["graph"],
+           "speedup": res["plain"] / res["batched"], "graph_speedup": res["plain"] / res["graph"],
+           "graph_capture_s": round(capture_s, 2), "graph_kernels": int(g_st[0]["launches"]),
+           "bits_equal_to_plain": bool(same), "warmup": 1 if warmup else 0}
+    out.update(product_errors(errs))
+    out["graph_errors"] = product_errors(g_errs)
+    if op_by_op:
+        out["op_by_op"] = "Alg. 2 op by op: one product per call, one match per launch sequence"
+        out["op_by_op_s"] = res["op_by_op"]
+        out["speedup_over_op_by_op"] = res["op_by_op"] / res["batched"]
+    return out
 
 
 def dense_layer_pt(stream, rot_base=16):
@@ -491,40 +545,42 @@ def dense_layer_pt(stream, rot_base=16):
             "ms": ms, "products_per_s": 1e3 / ms, "warmup": 0, "max_abs_err": err, "keygen_s": round(keygen_s, 2)}
 
 
-def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
+def serve_run(stream, count, dims, rate, seed=4, ntt=(5, 0, 0), project=2000):
     """Poisson stream of `count` requests (d from `dims`, sparsity U[0.5,0.95],
     remaining levels U{10..30}, 4 key sets) on the serving ring (N=2^16, L=31,
-    dnum=4): the continuous-batching server against the plain path, which runs
-    each request alone in arrival order with Alg. 2 op by op (one match per
-    launch sequence).  Latency = completion - arrival; at an offered rate
-    above both capacities, throughput = capacity."""
+    dnum=4): the continuous-batching server against the plain path, which
+    runs each request alone in arrival order with one
+    spfhe_sparse_matmul_ct_ct call.  Latency = completion - arrival, both arms
+    at the same offered rate.  Every served result is decrypted and compared
+    with FP64 and bit for bit with the plain path's result.  `project`: the
+    stated stream (that many requests of d in {64..512}) projected from its
+    exact match counts at the served match rate measured here."""
     import torch
     from paper_2604_11659_gb300 import params as gparams
     from paper_2604_11659_gb300 import spfhe as sp
     from paper_2604_11659_gb300 import synthetic
     reqs = synthetic.serving_stream(seed=seed, count=count, dims=dims, rate_per_s=rate)
     rec = reqs[0].case.ring
+    S = (1 << rec.log_n) // 2
     ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
     set_ntt(sp, ctx, ntt)
     keysets = [sp.spfhe_keygen(ctx, 700 + k) for k in range(4)]
     prods = [_encrypt_case(sp, ctx, keysets[r.key_set], r.case, r.level, rec.scale, 10 * i) for i, r in enumerate(reqs)]
     torch.cuda.synchronize()
     matches = 0
-    # plain: one request at a time, in arrival order, each alone, op by op
-    lat_plain = []
-    sp.spfhe_ctx_set_match_batch(ctx, 1)
+    # plain: one request at a time, in arrival order, each alone
+    lat_plain, plain_out = [], []
     t0 = time.perf_counter()
     for r, (Am, a, Bm, b, nc) in zip(reqs, prods):
         now = time.perf_counter() - t0
         if now < r.arrival_s:
             time.sleep(r.arrival_s - now)
         outs, st = sp.spfhe_sparse_matmul_ct_ct(ctx, keysets[r.key_set], Am, a, Bm, b, None, nc)
+        sp.spfhe_sync(ctx)
         matches += st["matches"]
         lat_plain.append((time.perf_counter() - t0) - r.arrival_s)
-        for h in outs:
-            sp.spfhe_ct_free(h)
+        plain_out.append(outs)
     plain_total = time.perf_counter() - t0
-    sp.spfhe_ctx_set_match_batch(ctx, 0)
     # served
     srv = sp.spfhe_server_create(ctx, 64 << 30)
     tickets = []
@@ -541,8 +597,16 @@ def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
     served_total = time.perf_counter() - t0
     sp.spfhe_server_destroy(srv)
     lat_served = [lat / 1e3 for _, lat in got]
-    for outs, _ in got:
-        for h in outs:
+    errs, same = [], True
+    for r, (outs, _), po in zip(reqs, got, plain_out):
+        c = r.case
+        C = decrypt_matrix(sp, ctx, keysets[r.key_set], outs, c.A.shape[0], c.B.shape[1], S)
+        D = C - c.A @ c.B
+        errs.append((float(np.max(np.abs(D))), float(np.sqrt(np.sum(D * D)))))
+        for hs, hp in zip(outs, po):
+            same = same and np.array_equal(sp.spfhe_ct_export(ctx, hs, 1 << rec.log_n),
+                                           sp.spfhe_ct_export(ctx, hp, 1 << rec.log_n))
+        for h in outs + po:
             sp.spfhe_ct_free(h)
     for Am, a, Bm, b, nc in prods:
         for h in a + b:
@@ -551,12 +615,42 @@ def serve_run(stream, count, dims, rate, seed=4, ntt=(0, 0, 0)):
         sp.spfhe_keys_free(k)
     sp.spfhe_ctx_destroy(ctx)
     q = lambda xs, p: float(np.percentile(np.array(xs) * 1e3, p))
-    return {"workload": "%d requests, Poisson %.1f/s, d in %s, sparsity U[0.5,0.95], levels U{10..30}, 4 key sets, "
-                        "N=2^16, L=31, dnum=4 (scaled from 2000 requests of d in {64..512})" % (count, rate, list(dims)),
-            "matches": matches, "plain_path": "each request alone in arrival order, one match per launch sequence",
-            "served": {"p50_ms": q(lat_served, 50), "p99_ms": q(lat_served, 99), "requests_per_s": count / served_total},
-            "plain": {"p50_ms": q(lat_plain, 50), "p99_ms": q(lat_plain, 99), "requests_per_s": count / plain_total},
-            "throughput_speedup": plain_total / served_total}
+    out = {"workload": "%d requests, Poisson %.1f/s, d in %s, sparsity U[0.5,0.95], levels U{10..30}, 4 key sets, "
+                       "N=2^16, L=31, dnum=4" % (count, rate, list(dims)),
+           "matches": matches, "plain_path": "each request alone in arrival order, one spfhe_sparse_matmul_ct_ct call",
+           "served": {"p50_ms": q(lat_served, 50), "p99_ms": q(lat_served, 99), "requests_per_s": count / served_total,
+                      "matches_per_s": matches / served_total},
+           "plain": {"p50_ms": q(lat_plain, 50), "p99_ms": q(lat_plain, 99), "requests_per_s": count / plain_total,
+                     "matches_per_s": matches / plain_total},
+           "throughput_speedup": plain_total / served_total, "bits_equal_to_plain": bool(same)}
+    out.update(product_errors(errs))
+    if project:
+        out["stated_stream_projection"] = project_stated_stream(project, matches / served_total)
+    return out
+
+
+def project_stated_stream(count, matches_per_s, seed=4):
+    """The stated serving stream (`count` requests, d in {64, 128, 256, 512},
+    sparsity U[0.5, 0.95], levels 10-30): exact match counts from the Alg. 1
+    planner, and the time it would take at a measured served match rate.  Its
+    requests are far larger than any bench run can complete (a d = 512
+    request at 50 % sparsity has 33.6 M matches), so it is projected, not run."""
+    from paper_2604_11659_gb300 import synthetic
+    reqs = synthetic.serving_stream(seed=seed, count=count)
+    per_d = {}
+    total = 0
+    for r in reqs:
+        A, B = r.case.A, r.case.B
+        m = int(sum(np.count_nonzero(A[:, k]) * np.count_nonzero(B[k, :]) for k in range(A.shape[1])))
+        total += m
+        d = A.shape[0]
+        per_d.setdefault(d, []).append(m)
+    return {"requests": count, "matches": total,
+            "mean_matches_by_d": {str(d): float(np.mean(v)) for d, v in sorted(per_d.items())},
+            "projected_hours_at_served_rate": total / matches_per_s / 3600.0,
+            "served_matches_per_s": matches_per_s,
+            "how": "exact match counts (sum over k of nnz(A[:, k]) nnz(B[k, :])) times the served match rate "
+                   "measured on the scaled stream above"}
 
 
 # ---------------------------------------------------------------------------
@@ -654,8 +748,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": val, "unit": "matmuls/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(args.workload, case, s.P.K, args.rot_base),
-                       "l2": "working set >> L2"},
+            "config": bench_config(workload_desc(args.workload, case, s.P.K, args.rot_base)),
             "cpu_baseline": {"value": val, "unit": "matmuls/s", "cores": cores, "kind": "oracle",
                              "sample": "per step: one sample of the per-match ops (%.1f s CPU), projected with "
                                        "exact op counts (%d matches)" % (cpu_total / args.steps, s.matches)},
@@ -710,8 +803,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-products", type=int, default=16)
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--batch128-products", type=int, default=3,
+                    help="128x128 products (N=2^16, sparsity U[0.90,0.95]) batched vs one call each (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--graph-steps", type=int, default=2,
                     help="timed launches of the headline product captured as one CUDA graph (0: skip)")
     ap.add_argument("--dense-layer", type=int, default=1,
@@ -765,13 +860,13 @@ def main():
 
     # measured ALU speed of light (register-resident microbenchmarks), outside the timed region
     try:
-        alu_meas = sp.spfhe_prof_alu_peak(g.ctx)
+        alu_meas = sp.spfhe_prof_alu_rates(g.ctx)
     except sp.SpfheError as exc:
         alu_meas = None
         print("ALU microbenchmark unavailable: %s" % exc, file=sys.stderr)
 
-    # timed region: device events on the context stream, per-kernel profile live
-    sp.spfhe_prof_enable(g.ctx, True)
+    # timed region: device events on the context stream, profiler off
+    sp.spfhe_prof_enable(g.ctx, False)
     launches0 = sp.spfhe_launch_count(g.ctx)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -794,12 +889,17 @@ def main():
     clocks = clk.summary()
     ms_total = ev0.elapsed_time(ev1)
     launches = sp.spfhe_launch_count(g.ctx) - launches0
-    prof = sp.spfhe_prof_all(g.ctx)
-    ks_info = sp.spfhe_prof_keyswitch(g.ctx)
-    sp.spfhe_prof_enable(g.ctx, False)
     err = g.check(last)
     frob = g.last_frobenius
     g.free(last)
+    # one more step with the per-kernel event profiler on (two events around
+    # every launch): the per-class breakdown and the roofline's kernel times
+    sp.spfhe_prof_enable(g.ctx, True)
+    outs, _ = g.step()
+    prof = sp.spfhe_prof_all(g.ctx)
+    ks_info = sp.spfhe_prof_keyswitch(g.ctx)
+    sp.spfhe_prof_enable(g.ctx, False)
+    g.free(outs)
     ms_total = max_over_ranks(dist, ms_total, dev)
     ms_step = ms_total / args.steps
     value = whole_job_rate(world, args.steps, ms_total / 1e3)
@@ -901,30 +1001,37 @@ def main():
         achieved = dd["work"] / (dd["ms"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tmulmod/s", "frac": achieved / peak,
-                "traffic": (ks_ntt_fwd_traffic(dd["work"], dd["bytes"], dd["launches"], g.n, g.rec.log_n)
+                "traffic": (ks_ntt_fwd_traffic(dd.get("limbs", (0.0, 0.0, 0.0)), dd["launches"])
                             if dom == "ks_ntt_fwd" and g.ntt_chunk[0] == NTT_FWD_DRAM_VARIANT else None),
                 "traffic_source": traffic_source(dom, g.ntt_chunk[0]),
+                "measured_on": "one profiled step after the timed region (CUDA events around every launch)",
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per 64-bit modmul" % sm_max,
                 "work_unit": "one 64-bit modular multiply (an NTT butterfly, or a base-conversion MAC)",
                 "work_per_launch": dd["work"] / max(1, dd["launches"]),
                 "algorithmic_bytes_per_launch": dd["bytes"] / max(1, dd["launches"]),
                 "hbm_gbs": dd["bytes"] / (dd["ms"] * 1e-3) / 1e9,
+                "algorithmic_bytes": "each transformed limb read once and written once (16 B per residue), plus "
+                                     "the limbs a fused epilogue reads and writes; the HBM round trip between "
+                                     "the two passes is implementation traffic",
                 "alu_microbench": alu_microbench(alu_meas, achieved if dom in NTT_CLASSES else None,
                                                  clocks.get("sm_mhz") or sm_max)}
     else:
         achieved = dd["bytes"] / (dd["ms"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src}
+    if roof.get("traffic"):
+        roof["traffic_over_algorithmic"] = roof["traffic"] / max(1.0, roof["algorithmic_bytes_per_launch"])
     ks_ms = sum(prof[c]["ms"] for c in KS_CLASSES)
     ks_calls, ks_bytes = ks_info
 
     line = {"metric": METRIC, "value": value, "unit": "matmuls/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload, case, g.K, args.rot_base),
-                       "matches": st["matches"], "ks_per_step": st["ks_relin"] + st["ks_align"] + st["ks_final"],
-                       "ntt_variant_split_chunk": list(g.ntt_chunk), "ntt_tuning_ms": g.ntt_tune,
-                       "l2": "inputs+keys >> 129 MB L2 (no flush)", "parallelism": "independent products per GPU"},
+            "config": bench_config(workload_desc(args.workload, case, g.K, args.rot_base)),
+            "step": {"matches": st["matches"], "ks_per_step": st["ks_relin"] + st["ks_align"] + st["ks_final"],
+                     "ks_relin": st["ks_relin"], "ks_align": st["ks_align"], "ks_final": st["ks_final"],
+                     "profiler": "off in the timed steps"},
+            "tuning": {"ntt_variant_split_chunk": list(g.ntt_chunk), "ntt_tuning_ms": g.ntt_tune},
             "e2e": {"value": e2e_val, "unit": "matmuls/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
             "max_abs_err": err, "frobenius_err": frob, "rotation_base": rot_base_info,
@@ -941,6 +1048,11 @@ def main():
     sp.spfhe_ctx_destroy(g.ctx)
     if args.batch_products > 0:
         line["batch"] = batch_vs_plain(stream, args.batch_products, (8, 16), ntt=g.ntt_chunk)
+    if args.batch128_products > 0:
+        # the metric's own product size: 128x128 at N=2^16, one warm-up-free
+        # run per arm (the workspaces were sized by the line above), no op-by-op arm
+        line["batch_128x128"] = batch_vs_plain(stream, args.batch128_products, (128,), seed=5, ntt=g.ntt_chunk,
+                                               sparsity=(0.90, 0.95), op_by_op=False, warmup=False)
     if args.serve_requests > 0:
         line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
     if args.dense_layer:

@@ -141,20 +141,21 @@ spfhe_status spfhe_ctx_set_ntt_chunk(spfhe_ctx *ctx, uint32_t limbs);
  * it. */
 spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
 
-/* Kernel variant of the two-pass NTT (n >= 2^12): 0 (default) = twiddles
- * read per butterfly stage from global memory at 3 CTAs per SM; 1 = the same
- * with the register budget of 2 CTAs per SM; 2 = as 1, with the second pass
- * copying its twiddles into shared memory asynchronously before its data
- * loads (about 64 KB of dynamic shared memory per CTA); 3 = as 0 with the
- * register budget of 4 CTAs per SM; 4 = as 3 with every 32x32-bit partial
- * product of the Shoup multiplications taken as separate low and high
- * halves instead of one 64-bit-result multiply.  EINVAL otherwise.
- * Results do not depend on it. */
+/* Kernel variant of the two-pass NTT (n >= 2^12): 0 = twiddles read per
+ * butterfly stage from global memory at 3 CTAs per SM; 1 = the same with the
+ * register budget of 2 CTAs per SM; 2 = as 1, with the second pass copying
+ * its twiddles into shared memory asynchronously before its data loads
+ * (about 64 KB of dynamic shared memory per CTA); 3 = as 0 with the register
+ * budget of 4 CTAs per SM; 4 = as 3 with every 32x32-bit partial product of
+ * the Shoup multiplications taken as separate low and high halves instead of
+ * one 64-bit-result multiply; 5 (default) = as 4 with a shorter quotient
+ * estimate (products in [0, 4q), intermediate values kept below 8q).
+ * EINVAL otherwise.  Results do not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
 /* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
  * the rescale's spread and last step run inside the forward transforms that
- * feed them (kernel variant 0, 3 or 4, n >= 2^12); 0: as separate kernels.  Results
+ * feed them (kernel variant 0, 3, 4 or 5, n >= 2^12); 0: as separate kernels.  Results
  * do not depend on it. */
 spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable);
 
@@ -172,6 +173,12 @@ uint64_t spfhe_launch_count(const spfhe_ctx *ctx);
 spfhe_status spfhe_prof_enable(spfhe_ctx *ctx, int enable);
 spfhe_status spfhe_prof_read(spfhe_ctx *ctx, int cls, uint64_t *launches, double *ms, double *bytes, double *work);
 int spfhe_prof_classes(void);
+/* For a transform class: limbs transformed since spfhe_prof_enable by pass
+ * kind (the transforms run in two passes over each limb): first passes,
+ * second passes, and second passes with a fused epilogue (ModDown's or the
+ * rescale's final step).  Counted whether or not the profiler is on. */
+spfhe_status spfhe_prof_transform_limbs(spfhe_ctx *ctx, int cls, double *first, double *second,
+                                        double *second_fused);
 const char *spfhe_prof_class_name(int cls);
 /* Key switching as a whole since the last spfhe_prof_enable: number of
  * key-switched polynomials and their algorithmic bytes (input polynomial,
@@ -195,6 +202,12 @@ spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes
  * graph capture), SPFHE_ENOMEM, SPFHE_ECUDA. */
 spfhe_status spfhe_prof_alu_peak(spfhe_ctx *ctx, double *butterflies_per_s, double *butterflies_split_per_s,
                                  double *imad_per_s, double *imad_wide_per_s);
+/* The same microbenchmarks with every butterfly form the transforms use:
+ * rates[0..2] = butterflies/s with the truncated-quotient Shoup product as
+ * wide products, as split halves, and with the shorter quotient (products in
+ * [0, 4q)); rates[3..5] = 32-bit multiply-adds per second with a 32-bit
+ * result, a 64-bit result, and the high half.  n >= 6. */
+spfhe_status spfhe_prof_alu_rates(spfhe_ctx *ctx, double *rates, size_t n);
 
 /* ---- keys ------------------------------------------------------------ */
 /* Sample a ternary secret, the relinearisation key and one rotation key per
@@ -450,13 +463,18 @@ spfhe_status spfhe_sparse_matmul_batch(spfhe_ctx *ctx, size_t n_req, const spfhe
 /* Continuous-batching server.  A worker thread owns the context until
  * spfhe_server_destroy: do not use the context (or its handles) from other
  * threads meanwhile, except through the server calls.  Between waves of
- * work the worker admits submitted requests in arrival order while their
- * result buffers fit hbm_budget_bytes (a request is always admitted when
- * nothing else runs) and mixes their work into the running batches;
- results
- * are bit-identical to running each request alone.  Operands and keys of a
- * submitted request must stay alive until spfhe_server_wait returns for it;
- * its metadata is copied at submission. */
+ * work the worker admits submitted requests in arrival order while
+ * hbm_budget_bytes holds the engine's shared batch buffers (their size at the
+ * highest level admitted so far) plus, for every admitted unfinished request,
+ * its result chunks and its mask (the private copy of a caller's mask, or the
+ * library's mask for its level when the context has none yet); a request is
+ * always admitted when nothing else runs.  Admitted work is mixed into the
+ * running batches; results are bit-identical to running each request alone.
+ * A wave that fails does not fail the requests in it: those whose last kernel
+ * had completed keep their results, the others are run again one at a time,
+ * each alone, and only a request that fails by itself reports its error.
+ * Operands and keys of a submitted request must stay alive until
+ * spfhe_server_wait returns for it; its metadata is copied at submission. */
 typedef struct spfhe_server spfhe_server;
 spfhe_status spfhe_server_create(spfhe_ctx *ctx, uint64_t hbm_budget_bytes, spfhe_server **out);
 spfhe_status spfhe_server_submit(spfhe_server *srv, const spfhe_matmul_req *req, uint64_t *ticket);
@@ -468,6 +486,17 @@ spfhe_status spfhe_server_wait(spfhe_server *srv, uint64_t ticket, spfhe_ct **C_
                                spfhe_stats *stats, double *latency_ms);
 /* Finish every submitted request, stop the worker, free unclaimed results. */
 spfhe_status spfhe_server_destroy(spfhe_server *srv);
+/* Host-side fault injection for tests of the failure handling above: every
+ * wave that would run work of request `ticket` fails with SPFHE_ECUDA before
+ * launching anything (no GPU fault is involved).  `ticket` may name a request
+ * not submitted yet (tickets are handed out 1, 2, 3, ... per server) or one
+ * still queued; EINVAL for a request already admitted or no longer known. */
+spfhe_status spfhe_server_inject_fault(spfhe_server *srv, uint64_t ticket);
+/* Admission bookkeeping: bytes reserved for the shared batch buffers, bytes
+ * held by admitted unfinished requests, and the number of requests re-run
+ * alone after a failed wave.  Any pointer may be NULL. */
+spfhe_status spfhe_server_info(spfhe_server *srv, uint64_t *workspace_reserved, uint64_t *in_use,
+                               uint64_t *retried);
 
 /* ---- products captured as one CUDA graph --------------------------------- */
 /* A product planned and captured once into a CUDA graph, launched as one unit

@@ -195,7 +195,7 @@ spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {
         need(ctx != nullptr, "null context");
-        need(variant <= 4, "NTT variant must be 0 to 4");
+        need(variant <= 5, "NTT variant must be 0 to 5");
         ctx->c.ntt_variant = (int)variant;
     });
 }
@@ -223,6 +223,22 @@ spfhe_status spfhe_prof_read(spfhe_ctx *ctx, int cls, uint64_t *launches, double
 }
 
 int spfhe_prof_classes(void) { return K_NCLASS; }
+
+spfhe_status spfhe_prof_transform_limbs(spfhe_ctx *ctx, int cls, double *first, double *second,
+                                        double *second_fused)
+{
+    try {
+        if (!ctx || cls < 0 || cls >= K_NCLASS) throw Error(SPFHE_EINVAL, "bad argument");
+        const Prof &p = ctx->c.prof;
+        if (first) *first = p.limbs[cls][0];
+        if (second) *second = p.limbs[cls][1];
+        if (second_fused) *second_fused = p.limbs[cls][2];
+        return SPFHE_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
 
 spfhe_status spfhe_prof_keyswitch(spfhe_ctx *ctx, uint64_t *calls, double *bytes)
 {

@@ -25,6 +25,37 @@ int match_batch_size(const Ctx &ctx)
 
 size_t chunks_for(long long count, int S) { return (size_t)std::max(1LL, (count + S - 1) / S); }
 
+uint64_t engine_workspace_bound(const Ctx &ctx, int ell)
+{
+    // limbs per batch item of every workspace slot a wave at level ell uses
+    // (run_wave, run_matches, rotate_batch, keyswitch_batch)
+    const uint64_t B = (uint64_t)match_batch_size(ctx);
+    const uint64_t l = (uint64_t)ell, K = (uint64_t)ctx.K;
+    const uint64_t beta = (l + ctx.alpha - 1) / ctx.alpha;
+    const uint64_t limbs = 2 * l        // WS_ALIGN (G = B alignment outputs)
+                           + 3 * l      // WS_TENSOR
+                           + 2 * l      // WS_RELIN_OUT
+                           + 2 * l      // WS_LEVEL1 (2 (ell-1), rounded up)
+                           + 2 * l      // WS_LEVEL2
+                           + 2 * l      // WS_RS_TMP
+                           + 2 * l      // WS_MISC
+                           + l          // WS_KS_COEF
+                           + beta * (l + K)   // WS_KS_EXT
+                           + 2 * (l + K)      // WS_KS_ACC
+                           + 2 * l      // WS_KS_CONV
+                           + l          // WS_ROT_TMP
+                           + 4 * l;     // WS_ROT_OUT_A, WS_ROT_OUT_B
+    return B * limbs * (uint64_t)ctx.n * sizeof(u64);
+}
+
+uint64_t job_mask_bytes(const Ctx &ctx, const Job &job)
+{
+    const int ell = job.Ach.empty() || !job.Ach[0] ? ctx.L : job.Ach[0]->level;
+    const uint64_t mask = (uint64_t)std::max(ell - 1, 1) * ctx.n * sizeof(u64);
+    if (job.mask0) return mask;
+    return ctx.masks.count(ell) ? 0 : mask;
+}
+
 Engine::Engine(Ctx &ctx) : ctx_(ctx) {}
 
 Engine::~Engine() = default;
@@ -224,6 +255,9 @@ bool Engine::step()
 void Engine::run_wave(int ell, LevelQueue &q)
 {
     Ctx &ctx = ctx_;
+    for (Job *j : order_)
+        if (j->inject_fault && !j->finished && j->ell == ell)
+            throw Error(SPFHE_ECUDA, "injected fault (host-side test hook) in a wave of job " + std::to_string(j->id));
     Runtime &rt = *ctx.rt;
     const int Bm = match_batch_size(ctx);
     const int G = Bm;

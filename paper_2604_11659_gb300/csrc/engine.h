@@ -39,6 +39,10 @@ struct Job {
     uint64_t st_matches = 0, st_relin = 0, st_align = 0, st_final = 0, st_rescales = 0, st_launches = 0;
     cudaEvent_t done_ev = nullptr;
     bool finished = false;
+    // host-side fault injection (tests of the serving loop's error
+    // isolation): any wave that would run this job's tasks throws SPFHE_ECUDA
+    // before launching anything
+    bool inject_fault = false;
 };
 
 class Engine {
@@ -97,6 +101,16 @@ void fill_job(Job &job, const Keys &keys, const spfhe_sparse_meta &A, Ct *const 
               const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, size_t nC);
 // free a job's private mask copy (and its results when free_results)
 void release_job(Ctx &ctx, Job &job, bool free_results);
+// after release_job(.., true): clear what Engine::add and the waves filled
+// in, so the job can be added to an engine again
+void reset_job(Job &job);
+// Device memory an engine's waves at operand level ell may hold in the
+// context's workspace cache (every batch buffer at its largest), bytes.
+uint64_t engine_workspace_bound(const Ctx &ctx, int ell);
+// Device memory Engine::add allocates for a job beyond its result chunks: the
+// Montgomery copy of a caller's mask, or the library's own level mask when
+// the context has none yet (bytes).
+uint64_t job_mask_bytes(const Ctx &ctx, const Job &job);
 size_t chunks_for(long long count, int S);
 // checks shared by the ct x ct products (metadata, chunk counts, levels,
 // scales); returns the operands' level and their product's result scale

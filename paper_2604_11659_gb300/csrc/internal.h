@@ -81,6 +81,9 @@ struct Prof {
     uint64_t launches[K_NCLASS] = {};
     uint64_t timed[K_NCLASS] = {};
     double bytes[K_NCLASS] = {}, work[K_NCLASS] = {}, ms[K_NCLASS] = {};
+    // transform classes: limbs by pass kind (0 = first pass, 1 = second
+    // pass, 2 = second pass with a fused epilogue)
+    double limbs[K_NCLASS][3] = {};
     // key switching as a whole: calls and algorithmic bytes (input poly,
     // output pair, and each key stream once per item group sharing it)
     uint64_t ks_calls = 0;
@@ -107,7 +110,7 @@ struct Ctx {
     int match_batch = 0;             // matches per batch (0: default for the ring size)
     int ntt_chunk = 0;               // limbs per pass-A/pass-B launch pair (0: whole batch)
     int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
-    int ntt_variant = 0;             // radix-16 kernel variant (0 to 3)
+    int ntt_variant = 5;             // radix-16 kernel variant (0 to 5)
     bool fuse_epilogues = true;      // ModDown / rescale epilogues inside the forward transform
     // while a CUDA graph is being captured: its own buffers (graph.cpp)
     struct Capture *cap = nullptr;

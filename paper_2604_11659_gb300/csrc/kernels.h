@@ -129,6 +129,17 @@ void add_gadget(Ctx &ctx, u64 *out, const u64 *sprime, int lo, int hi);
 cudaEvent_t prof_begin(Ctx &ctx);
 void prof_end(Ctx &ctx, cudaEvent_t start, int cls, double bytes, double work, const char *what);
 void prof_reset(Ctx &ctx, bool on);
+// count `limbs` transformed limbs of pass kind `kind` (see Prof::limbs)
+void prof_limbs(Ctx &ctx, int cls, int kind, double limbs);
+// While one of these lives, launches made by the constructing thread record no
+// profiler events (calls that must create no CUDA events of their own); the
+// context's profiler switch itself is left untouched.
+struct ProfSuppress {
+    ProfSuppress();
+    ~ProfSuppress();
+    ProfSuppress(const ProfSuppress &) = delete;
+    ProfSuppress &operator=(const ProfSuppress &) = delete;
+};
 void prof_collect(Ctx &ctx);
 void prof_destroy(Ctx &ctx);
 const char *kernel_class_name(int cls);

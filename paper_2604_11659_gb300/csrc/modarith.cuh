@@ -140,11 +140,54 @@ __device__ __forceinline__ u64 mul_shoup3s(u64 x, u64 w, u64 wp, u64 nq)
     return r;
 }
 
-template <bool SPLIT> __device__ __forceinline__ u64 mul_shoup3v(u64 x, u64 w, u64 wp, u64 nq)
+// Shoup product whose quotient keeps only the high halves of the two middle
+// partial products of x * w': Q' = x1 a1 + hi(x1 a0) + hi(x0 a1).  The
+// dropped parts (the two low halves times 2^32, and x0 a0) are each below
+// 2^64, so Q' is at most two below floor(x w' / 2^64) and, as
+// x*w - floor(x w' / 2^64)*q lies in [0, 2q), the result x*w - Q'*q lies in [0, 4q) for
+// any x < 2^64 (q < 2^62).  Twelve single-word multiplies (seven low halves,
+// five high halves): two fewer than mul_shoup3s and one carry chain shorter.
+__device__ __forceinline__ u64 mul_shoup4s(u64 x, u64 w, u64 wp, u64 nq)
 {
-    if constexpr (SPLIT) return mul_shoup3s(x, w, wp, nq);
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 x0, x1, a0, a1, w0, w1, n0, n1, h0, h1, q0, q1, r0, r1;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\t"
+        "mov.b64 {a0, a1}, %3;\n\t"
+        "mul.hi.u32 h0, x1, a0;\n\t"
+        "mul.hi.u32 h1, x0, a1;\n\t"
+        "add.cc.u32 h0, h0, h1;\n\t"
+        "addc.u32 h1, 0, 0;\n\t"
+        "mad.lo.cc.u32 q0, x1, a1, h0;\n\t"
+        "madc.hi.u32 q1, x1, a1, h1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.lo.u32 r0, x0, w0;\n\t"
+        "mul.hi.u32 r1, x0, w0;\n\t"
+        "mad.lo.cc.u32 r0, q0, n0, r0;\n\t"
+        "madc.hi.u32 r1, q0, n0, r1;\n\t"
+        "mad.lo.u32 r1, x0, w1, r1;\n\t"
+        "mad.lo.u32 r1, x1, w0, r1;\n\t"
+        "mad.lo.u32 r1, q0, n1, r1;\n\t"
+        "mad.lo.u32 r1, q1, n0, r1;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(x), "l"(w), "l"(wp), "l"(nq));
+    return r;
+}
+
+// Butterfly arithmetic of the transform kernels: AR = 0 mul_shoup3 (wide
+// partial products), 1 mul_shoup3s (split halves), both with results in
+// [0, 3q); AR = 2 mul_shoup4s, results in [0, 4q).
+template <int AR> __device__ __forceinline__ u64 mul_shoup_ar(u64 x, u64 w, u64 wp, u64 nq)
+{
+    if constexpr (AR == 2) return mul_shoup4s(x, w, wp, nq);
+    else if constexpr (AR == 1) return mul_shoup3s(x, w, wp, nq);
     else return mul_shoup3(x, w, wp, nq);
 }
+// multiple of q that bounds mul_shoup_ar<AR>'s result
+template <int AR> constexpr u64 shoup_bound() { return AR == 2 ? 4 : 3; }
 
 // Montgomery reduction of T = (hi, lo) < q * 2^64: returns T * 2^-64 mod q in [0, q)
 __device__ __forceinline__ u64 redc(U128 t, u64 q, u64 qneg_inv)

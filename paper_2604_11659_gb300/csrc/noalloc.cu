@@ -92,44 +92,39 @@ extern "C" spfhe_status spfhe_rescale_noalloc(spfhe_ctx *ctx, const uint64_t *in
                                           " scratch words; the fixed scratch holds " + std::to_string(kNoAllocWords));
         u64 *top = scratch_on_device(c.device);
         u64 *spread = top + n;
-        // the profiler would create CUDA events; keep it off for this call
-        const bool prof_was_on = c.prof.on;
-        c.prof.on = false;
+        // the profiler would create CUDA events: none are recorded for this
+        // call's launches (a per-thread guard; the context's own profiler
+        // switch, which another thread may be reading, is not touched)
+        ProfSuppress quiet;
         const int threads = 256, blocks = (int)((n + threads - 1) / threads);
         const u64 qt = c.mods[ell - 1];
-        try {
-            for (int b = 0; b < 2; ++b) {
-                const u64 *cin = reinterpret_cast<const u64 *>(in) + (size_t)b * ell * n;
-                u64 *cout = reinterpret_cast<u64 *>(out) + (size_t)b * (ell - 1) * n;
-                k_na_copy<<<blocks, threads, 0, c.stream>>>((int)n, cin + (size_t)(ell - 1) * n, top);
-                prof_end(c, nullptr, K_RESCALE, 16.0 * n, 0.0, "rescale (no alloc) copy");
-                LimbMap tm;
-                tm.nl = 1;
-                tm.off[0] = 0;
-                tm.mi[0] = ell - 1;
-                ntt_inverse(c, Batch{top, 0, 1, nullptr}, tm);
-                for (int i = 0; i < ell - 1; ++i) {
-                    const ModConst &m = c.mc[i];
-                    const u64 qi = c.mods[i];
-                    const u64 qt_mod = qt % qi;
-                    const u64 inv = invmod_host(qt_mod, qi);
-                    k_na_spread<<<blocks, threads, 0, c.stream>>>((int)n, top, qt, qt_mod, m, spread);
-                    prof_end(c, nullptr, K_RESCALE, 16.0 * n, 1.0 * n, "rescale (no alloc) spread");
-                    LimbMap sm;
-                    sm.nl = 1;
-                    sm.off[0] = 0;
-                    sm.mi[0] = i;
-                    ntt_forward(c, Batch{spread, 0, 1, nullptr}, sm);
-                    k_na_final<<<blocks, threads, 0, c.stream>>>((int)n, cin + (size_t)i * n, spread, inv,
-                                                                 shoup_pre(inv, qi), qi, cout + (size_t)i * n);
-                    prof_end(c, nullptr, K_RESCALE, 24.0 * n, 1.0 * n, "rescale (no alloc) final");
-                }
+        for (int b = 0; b < 2; ++b) {
+            const u64 *cin = reinterpret_cast<const u64 *>(in) + (size_t)b * ell * n;
+            u64 *cout = reinterpret_cast<u64 *>(out) + (size_t)b * (ell - 1) * n;
+            k_na_copy<<<blocks, threads, 0, c.stream>>>((int)n, cin + (size_t)(ell - 1) * n, top);
+            prof_end(c, nullptr, K_RESCALE, 16.0 * n, 0.0, "rescale (no alloc) copy");
+            LimbMap tm;
+            tm.nl = 1;
+            tm.off[0] = 0;
+            tm.mi[0] = ell - 1;
+            ntt_inverse(c, Batch{top, 0, 1, nullptr}, tm);
+            for (int i = 0; i < ell - 1; ++i) {
+                const ModConst &m = c.mc[i];
+                const u64 qi = c.mods[i];
+                const u64 qt_mod = qt % qi;
+                const u64 inv = invmod_host(qt_mod, qi);
+                k_na_spread<<<blocks, threads, 0, c.stream>>>((int)n, top, qt, qt_mod, m, spread);
+                prof_end(c, nullptr, K_RESCALE, 16.0 * n, 1.0 * n, "rescale (no alloc) spread");
+                LimbMap sm;
+                sm.nl = 1;
+                sm.off[0] = 0;
+                sm.mi[0] = i;
+                ntt_forward(c, Batch{spread, 0, 1, nullptr}, sm);
+                k_na_final<<<blocks, threads, 0, c.stream>>>((int)n, cin + (size_t)i * n, spread, inv,
+                                                             shoup_pre(inv, qi), qi, cout + (size_t)i * n);
+                prof_end(c, nullptr, K_RESCALE, 24.0 * n, 1.0 * n, "rescale (no alloc) final");
             }
-        } catch (...) {
-            c.prof.on = prof_was_on;
-            throw;
         }
-        c.prof.on = prof_was_on;
         return SPFHE_OK;
     } catch (const Error &e) {
         set_last_error(e.what());

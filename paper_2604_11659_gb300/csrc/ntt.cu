@@ -12,6 +12,12 @@
 //     takes 16 adjacent columns so every row read is a 128-byte segment;
 //   pass B covers stages [PA, log_n): contiguous tiles of 2^(log_n-PA).
 // Residues are kept fully reduced in [0, q) between stages.
+//
+// Algorithmic bytes credited to the profiler: a transform reads its limb once
+// and writes it once (8 B per residue each way), split as the read in the
+// first pass and the write in the second; the round trip between the passes
+// is implementation traffic and is not credited.  A fused epilogue adds the
+// limbs it reads and writes.
 #include <atomic>
 
 #include "kernels.h"
@@ -265,35 +271,35 @@ __device__ __forceinline__ void r16_load_tw(ulonglong2 (&wt)[16], int t, const u
 // all values by 3q, so after the log_n <= 17 stages of both passes they lie
 // in [0, 52q) (< 2^64) and pass B reduces them once at the end.  Otherwise
 // values stay in [0, 6q): x is first brought to [0, 3q).
-template <int P, int RND, int l, bool LAZY, bool SM, bool SPL = false>
+template <int P, int RND, int l, bool LAZY, bool SM, int AR = 0>
 __device__ __forceinline__ void r16_fwd_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt, int ltile)
 {
     constexpr int Q = r16_q<P, RND>();
     constexpr int half = 1 << (Q - 1 - l);
-    const u64 q3 = 3 * q, nq = 0 - q;
+    const u64 qb = shoup_bound<AR>() * q, nq = 0 - q;
     ulonglong2 wt[16];
     r16_load_tw<P, RND, Q, l, SM>(wt, t, w2, stage0, btile, smt, ltile);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (i & half) continue;
         const ulonglong2 w = wt[i >> (Q - l)];
-        const u64 x = LAZY ? v[i] : csub(v[i], q3);
-        const u64 y = mul_shoup3v<SPL>(v[i + half], w.x, w.y, nq);
+        const u64 x = LAZY ? v[i] : csub(v[i], qb);
+        const u64 y = mul_shoup_ar<AR>(v[i + half], w.x, w.y, nq);
         v[i] = x + y;
-        v[i + half] = x - y + q3;
+        v[i + half] = x - y + qb;
     }
 }
 
 // PRE: the stage's twiddles were loaded ahead into `pre`
-template <int P, int RND, int l, bool SM, bool PRE = false, bool SPL = false>
+template <int P, int RND, int l, bool SM, bool PRE = false, int AR = 0>
 __device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt, int ltile,
                                               const ulonglong2 (*pre)[16] = nullptr)
 {
     constexpr int Q = r16_q<P, RND>();
     constexpr int half = 1 << (Q - 1 - l);
-    const u64 q3 = 3 * q, nq = 0 - q;
+    const u64 qb = shoup_bound<AR>() * q, nq = 0 - q;
     ulonglong2 wt[16];
     if constexpr (PRE) {
 #pragma unroll
@@ -306,40 +312,42 @@ __device__ __forceinline__ void r16_inv_stage(u64 (&v)[16], int t, const ulonglo
         if (i & half) continue;
         const ulonglong2 w = wt[i >> (Q - l)];
         const u64 x = v[i], y = v[i + half];
-        v[i] = csub(x + y, q3);
-        v[i + half] = mul_shoup3v<SPL>(x - y + q3, w.x, w.y, nq);
+        v[i] = csub(x + y, qb);
+        v[i + half] = mul_shoup_ar<AR>(x - y + qb, w.x, w.y, nq);
     }
 }
 
 // Lazy butterflies (Harvey's scheme with the [0, 3q) products of
 // mul_shoup3): forward values stay below 6q (52q on the reduction-free path),
 // inverse values in [0, 3q); only the last pass reduces to [0, q).
-template <int P, int RND, bool LAZY, bool SM = false, bool SPL = false>
+template <int P, int RND, bool LAZY, bool SM = false, int AR = 0>
 __device__ __forceinline__ void r16_fwd_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt = nullptr,
                                               int ltile = 0)
 {
     constexpr int Q = r16_q<P, RND>();
-    r16_fwd_stage<P, RND, 0, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 1) r16_fwd_stage<P, RND, 1, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 2) r16_fwd_stage<P, RND, 2, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
-    if constexpr (Q > 3) r16_fwd_stage<P, RND, 3, LAZY, SM, SPL>(v, t, w2, q, stage0, btile, smt, ltile);
+    r16_fwd_stage<P, RND, 0, LAZY, SM, AR>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 1) r16_fwd_stage<P, RND, 1, LAZY, SM, AR>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 2) r16_fwd_stage<P, RND, 2, LAZY, SM, AR>(v, t, w2, q, stage0, btile, smt, ltile);
+    if constexpr (Q > 3) r16_fwd_stage<P, RND, 3, LAZY, SM, AR>(v, t, w2, q, stage0, btile, smt, ltile);
 }
 
-// moduli below this take the reduction-free forward butterflies
-constexpr u64 kLazyFwdBound = 1ull << 58;
+// moduli below this take the reduction-free forward butterflies: values grow
+// by shoup_bound<AR>() q per stage from [0, q), so after the 17 stages of the
+// largest transform they stay below 52q (AR 0, 1) or 69q (AR 2) < 2^64
+template <int AR> constexpr u64 lazy_fwd_bound() { return AR == 2 ? 1ull << 57 : 1ull << 58; }
 
 // PRE: the twiddles of the round's first stage (l = Q - 1) are in `pre`
-template <int P, int RND, bool SM = false, bool PRE = false, bool SPL = false>
+template <int P, int RND, bool SM = false, bool PRE = false, int AR = 0>
 __device__ __forceinline__ void r16_inv_round(u64 (&v)[16], int t, const ulonglong2 *__restrict__ w2, u64 q,
                                               int stage0, int btile, const ulonglong2 *smt = nullptr,
                                               int ltile = 0, const ulonglong2 (*pre)[16] = nullptr)
 {
     constexpr int Q = r16_q<P, RND>();
-    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM, PRE, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM, PRE && Q == 3, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM, PRE && Q == 2, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
-    r16_inv_stage<P, RND, 0, SM, PRE && Q == 1, SPL>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 3) r16_inv_stage<P, RND, 3, SM, PRE, AR>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 2) r16_inv_stage<P, RND, 2, SM, PRE && Q == 3, AR>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    if constexpr (Q > 1) r16_inv_stage<P, RND, 1, SM, PRE && Q == 2, AR>(v, t, w2, q, stage0, btile, smt, ltile, pre);
+    r16_inv_stage<P, RND, 0, SM, PRE && Q == 1, AR>(v, t, w2, q, stage0, btile, smt, ltile, pre);
 }
 
 // shared-memory slot of tile element j (pass B layout; pad one word per 16)
@@ -362,9 +370,11 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 //      asynchronous copies issued before its data loads;
 //   3: as 0 with the register budget of 4 CTAs per SM;
 //   4: as 3 with the Shoup products split into single-word halves
-//      (mul_shoup3s; the same bits).
-template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V == 3 || V == 4 ? 4 : 2); }
-template <int V> constexpr bool r16_split() { return V == 4; }
+//      (mul_shoup3s; the same bits);
+//   5: as 4 with the quotient's low middle halves dropped (mul_shoup4s,
+//      products in [0, 4q); the transforms' outputs are the same residues).
+template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V >= 3 ? 4 : 2); }
+template <int V> constexpr int r16_arith() { return V == 5 ? 2 : (V == 4 ? 1 : 0); }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -389,7 +399,7 @@ __device__ __forceinline__ void r16_prefetch_wait()
     __syncthreads();
 }
 
-template <int P, bool LAZY, int MODE, bool SPL = false>
+template <int P, bool LAZY, int MODE, int AR = 0>
 __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n,
                                              const FuseArgs &f, const ModConst *__restrict__ mc)
 {
@@ -417,14 +427,14 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol];
     }
-    r16_fwd_round<P, 0, LAZY, false, SPL>(v, t, w2, q, 0, 0);
+    r16_fwd_round<P, 0, LAZY, false, AR>(v, t, w2, q, 0, 0);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1, LAZY, false, SPL>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 1, LAZY, false, AR>(v, t, w2, q, 0, 0);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -433,7 +443,7 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2, LAZY, false, SPL>(v, t, w2, q, 0, 0);
+        r16_fwd_round<P, 2, LAZY, false, AR>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol] = v[i];
@@ -450,12 +460,12 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
-    constexpr bool SPL = r16_split<V>();
-    if (q < kLazyFwdBound) fwd16_a_body<P, true, MODE, SPL>(sm, p, q, w2, log_n, f, mc);
-    else fwd16_a_body<P, false, MODE, SPL>(sm, p, q, w2, log_n, f, mc);
+    constexpr int AR = r16_arith<V>();
+    if (q < lazy_fwd_bound<AR>()) fwd16_a_body<P, true, MODE, AR>(sm, p, q, w2, log_n, f, mc);
+    else fwd16_a_body<P, false, MODE, AR>(sm, p, q, w2, log_n, f, mc);
 }
 
-template <int P, bool LAZY, bool SM, int MODE = kFuseNone, bool SPL = false>
+template <int P, bool LAZY, bool SM, int MODE = kFuseNone, int AR = 0>
 __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m, const ulonglong2 *__restrict__ w2,
                                              int PA, const ulonglong2 *smt, const FuseArgs &f = FuseArgs{},
                                              int log_n = 0)
@@ -471,14 +481,14 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = tp[r16_index<P, 0>(t, i)];
     if constexpr (SM) r16_prefetch_wait();
-    r16_fwd_round<P, 0, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
+    r16_fwd_round<P, 0, LAZY, SM, AR>(v, t, w2, q, PA, btile, smt, tile);
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
-        r16_fwd_round<P, 1, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
+        r16_fwd_round<P, 1, LAZY, SM, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 2) {
         __syncthreads();
@@ -487,7 +497,7 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
-        r16_fwd_round<P, 2, LAZY, SM, SPL>(v, t, w2, q, PA, btile, smt, tile);
+        r16_fwd_round<P, 2, LAZY, SM, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     // the last round holds 16 contiguous elements per thread: stage through
     // shared memory so the global stores are coalesced
@@ -563,17 +573,18 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a,
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
-    constexpr bool SPL = r16_split<V>();
+    constexpr int AR = r16_arith<V>();
+    constexpr u64 LB = lazy_fwd_bound<AR>();
     if constexpr (MODE != kFuseNone) {
-        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, MODE, SPL>(sm, p, m, w2, PA, nullptr, f, log_n);
-        else fwd16_b_body<P, false, false, MODE, SPL>(sm, p, m, w2, PA, nullptr, f, log_n);
+        if (m.q < LB) fwd16_b_body<P, true, false, MODE, AR>(sm, p, m, w2, PA, nullptr, f, log_n);
+        else fwd16_b_body<P, false, false, MODE, AR>(sm, p, m, w2, PA, nullptr, f, log_n);
     } else if constexpr (V == 2) {
         r16_prefetch_tw<P>(smt, w2, PA, (int)(((size_t)blockIdx.x * kElems) >> P));
-        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
+        if (m.q < LB) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
         else fwd16_b_body<P, false, true>(sm, p, m, w2, PA, smt);
     } else {
-        if (m.q < kLazyFwdBound) fwd16_b_body<P, true, false, kFuseNone, SPL>(sm, p, m, w2, PA, nullptr);
-        else fwd16_b_body<P, false, false, kFuseNone, SPL>(sm, p, m, w2, PA, nullptr);
+        if (m.q < LB) fwd16_b_body<P, true, false, kFuseNone, AR>(sm, p, m, w2, PA, nullptr);
+        else fwd16_b_body<P, false, false, kFuseNone, AR>(sm, p, m, w2, PA, nullptr);
     }
 }
 
@@ -585,7 +596,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     __shared__ u64 sm[r16_smem_words_b<P>()];
     extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
     constexpr bool SM = V == 2;
-    constexpr bool SPL = r16_split<V>();
+    constexpr int AR = r16_arith<V>();
     constexpr int TPT = 1 << (P - 4);
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
@@ -619,7 +630,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
-    r16_inv_round<P, R - 1, SM, !SM, SPL>(v, t, w2, q, PA, btile, smt, tile, &wpre);
+    r16_inv_round<P, R - 1, SM, !SM, AR>(v, t, w2, q, PA, btile, smt, tile, &wpre);
     if constexpr (R > 2) {
         __syncthreads();
 #pragma unroll
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2, SM, false, SPL>(v, t, w2, q, PA, btile, smt, tile);
+        r16_inv_round<P, R - 2, SM, false, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 1) {
         __syncthreads();
@@ -636,7 +647,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0, SM, false, SPL>(v, t, w2, q, PA, btile, smt, tile);
+        r16_inv_round<P, 0, SM, false, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     u64 *tp = p + e0 + ((size_t)tile << P);
 #pragma unroll
@@ -659,18 +670,18 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
     const int lg_ncols = log_n - P;
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
-    constexpr bool SPL = r16_split<V>();
+    constexpr int AR = r16_arith<V>();
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p[((size_t)r16_index<P, R - 1>(t, i) << lg_ncols) + gcol];
-    r16_inv_round<P, R - 1, false, false, SPL>(v, t, w2, q, 0, 0);
+    r16_inv_round<P, R - 1, false, false, AR>(v, t, w2, q, 0, 0);
     if constexpr (R > 2) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_a<P>(col, r16_index<P, R - 1>(t, i))] = v[i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, R - 2>(t, i))];
-        r16_inv_round<P, R - 2, false, false, SPL>(v, t, w2, q, 0, 0);
+        r16_inv_round<P, R - 2, false, false, AR>(v, t, w2, q, 0, 0);
         __syncthreads();
     }
     if constexpr (R > 1) {
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))];
-        r16_inv_round<P, 0, false, false, SPL>(v, t, w2, q, 0, 0);
+        r16_inv_round<P, 0, false, false, AR>(v, t, w2, q, 0, 0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -730,7 +741,7 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variants 0, 3 and 4)
+// transforms with a fused prologue / epilogue (kernel variants 0, 3, 4 and 5)
 template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
@@ -746,13 +757,15 @@ template <int P, int V> struct R16FusedV {
 template <int P> struct R16Fused {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_a(g, s, a, c, mode, f);
+        if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_a(g, s, a, c, mode, f);
+        else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
         else R16FusedV<P, 0>::fwd_a(g, s, a, c, mode, f);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_b(g, s, a, c, PA, mode, f);
+        if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_b(g, s, a, c, PA, mode, f);
+        else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
         else R16FusedV<P, 0>::fwd_b(g, s, a, c, PA, mode, f);
     }
@@ -767,6 +780,7 @@ template <int P> struct R16Launch {
         case 2: f(R16LaunchV<P, 2>{}); break;
         case 3: f(R16LaunchV<P, 3>{}); break;
         case 4: f(R16LaunchV<P, 4>{}); break;
+        case 5: f(R16LaunchV<P, 5>{}); break;
         default: throw Error(SPFHE_EINVAL, "no such NTT variant");
         }
     }
@@ -903,12 +917,14 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
             {
                 cudaEvent_t t0_ = prof_begin(ctx);
                 r16_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, ca, ctx); });
-                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt fwd A");
+                prof_end(ctx, t0_, cls, 8.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt fwd A");
+                prof_limbs(ctx, cls, 0, (double)cm.nl * cb.items);
             }
             {
                 cudaEvent_t t0_ = prof_begin(ctx);
                 r16_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, ca, ctx, PA); });
-                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt fwd B");
+                prof_end(ctx, t0_, cls, 8.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt fwd B");
+                prof_limbs(ctx, cls, 1, (double)cm.nl * cb.items);
             }
         });
         return;
@@ -917,18 +933,20 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt fwd A");
+        prof_limbs(ctx, cls, 0, (double)map.nl * b.items);
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_fwd_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.tw, ctx.dt.twp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt fwd B");
+        prof_limbs(ctx, cls, 1, (double)map.nl * b.items);
     }
 }
 
 bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f)
 {
-    if (ctx.log_n < 12 || (ctx.ntt_variant != 0 && ctx.ntt_variant != 3 && ctx.ntt_variant != 4) || b.ids)
+    if (ctx.log_n < 12 || ctx.ntt_variant == 1 || ctx.ntt_variant == 2 || b.ids)
         return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
@@ -939,15 +957,23 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         r16_fused_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, a, ctx, mode, f); });
-        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items,
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items,
                  mode == kFuseRescale ? "ntt fwd A + rescale spread" : "ntt fwd A");
+        prof_limbs(ctx, cls, 0, (double)map.nl * b.items);
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         r16_fused_dispatch(PB, [&](auto L) { decltype(L)::fwd_b(grid, ctx.stream, a, ctx, PA, mode, f); });
-        prof_end(ctx, t0_, cls, (mode == kFuseModDown ? 40.0 : 32.0) * ctx.n * map.nl * b.items,
+        // epilogue: ModDown reads acc, the base limbs it adds (both
+        // polynomials, or only c0 for a rotation) and writes out; the rescale
+        // reads its input limb and writes out
+        const double base_limbs = !f.base ? 0.0 : (f.base_c1 ? 1.0 : 0.5) * map.nl;
+        const double epi = mode == kFuseModDown ? 16.0 * ctx.n * map.nl + 8.0 * ctx.n * base_limbs
+                                                : 16.0 * ctx.n * map.nl;
+        prof_end(ctx, t0_, cls, epi * b.items,
                  0.5 * ctx.n * PB * map.nl * b.items,
                  mode == kFuseRescale ? "ntt fwd B + rescale final" : "ntt fwd B + moddown final");
+        prof_limbs(ctx, cls, 2, (double)map.nl * b.items);
     }
     return true;
 }
@@ -967,12 +993,14 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
             {
                 cudaEvent_t t0_ = prof_begin(ctx);
                 r16_dispatch(PB, [&](auto L) { decltype(L)::inv_b(grid, ctx.stream, ca, ctx, PA); });
-                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt inv B");
+                prof_end(ctx, t0_, cls, 8.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PB * cm.nl * cb.items, "ntt inv B");
+                prof_limbs(ctx, cls, 0, (double)cm.nl * cb.items);
             }
             {
                 cudaEvent_t t0_ = prof_begin(ctx);
                 r16_dispatch(PA, [&](auto L) { decltype(L)::inv_a(grid, ctx.stream, ca, ctx); });
-                prof_end(ctx, t0_, cls, 16.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt inv A");
+                prof_end(ctx, t0_, cls, 8.0 * ctx.n * cm.nl * cb.items, 0.5 * ctx.n * PA * cm.nl * cb.items, "ntt inv A");
+                prof_limbs(ctx, cls, 1, (double)cm.nl * cb.items);
             }
         });
         return;
@@ -981,12 +1009,14 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_b<<<gb, kThreads, g.smem_b, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA, g.lgE);
-        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * (ctx.log_n - g.PA) * map.nl * b.items, "ntt inv B");
+        prof_limbs(ctx, cls, 0, (double)map.nl * b.items);
     }
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         k_inv_a<<<ga, kThreads, g.smem_a, ctx.stream>>>(a, ctx.dt.mc, ctx.dt.itw, ctx.dt.itwp, ctx.log_n, g.PA);
-        prof_end(ctx, t0_, cls, 16.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
+        prof_limbs(ctx, cls, 1, (double)map.nl * b.items);
     }
 }
 

@@ -14,10 +14,16 @@ const char *kernel_class_name(int cls)
     return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
 }
 
+// per-thread depth of live ProfSuppress guards
+static thread_local int tl_prof_suppress = 0;
+
+ProfSuppress::ProfSuppress() { ++tl_prof_suppress; }
+ProfSuppress::~ProfSuppress() { --tl_prof_suppress; }
+
 cudaEvent_t prof_begin(Ctx &ctx)
 {
     Prof &p = ctx.prof;
-    if (!p.on) return nullptr;
+    if (!p.on || tl_prof_suppress) return nullptr;
     if (p.used + 2 > p.pool.size()) {
         for (int i = 0; i < 256; ++i) {
             cudaEvent_t e;
@@ -45,6 +51,11 @@ void prof_end(Ctx &ctx, cudaEvent_t start, int cls, double bytes, double work, c
     p.recs.push_back(ProfRec{cls, start, b});
 }
 
+void prof_limbs(Ctx &ctx, int cls, int kind, double limbs)
+{
+    if (cls >= 0 && cls < K_NCLASS && kind >= 0 && kind < 3) ctx.prof.limbs[cls][kind] += limbs;
+}
+
 void prof_reset(Ctx &ctx, bool on)
 {
     Prof &p = ctx.prof;
@@ -56,6 +67,7 @@ void prof_reset(Ctx &ctx, bool on)
     for (int c = 0; c < K_NCLASS; ++c) {
         p.launches[c] = 0;
         p.bytes[c] = p.work[c] = p.ms[c] = 0;
+        p.limbs[c][0] = p.limbs[c][1] = p.limbs[c][2] = 0;
         p.timed[c] = 0;
     }
 }

@@ -2,16 +2,22 @@
 // the task engine (engine.h).
 //
 // Serving: a worker thread owns the context while the server lives.  Between
-// waves it admits queued requests whose result buffers fit the HBM budget
-// (operands and keys are already resident; the engine's batch buffers are
-// shared), plans them into the engine, and runs the next wave, so requests
-// that arrive while others are on the GPU join the same batches.  A
+// waves it admits queued requests while the HBM budget holds the engine's
+// batch buffers (reserved once, at their size for the highest admitted level)
+// plus every admitted request's result chunks and mask (operands and keys are
+// already resident), plans them into the engine, and runs the next wave, so
+// requests that arrive while others are on the GPU join the same batches.  A
 // request's completion is the CUDA event recorded after its last
-// accumulation; the worker polls these events and timestamps completions.
+// accumulation; the worker polls these events and timestamps completions.  A
+// wave that fails does not fail the requests in it: completed ones keep their
+// results and the rest run again alone, so only a request that fails by
+// itself reports an error.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 
 #include "engine.h"
@@ -81,7 +87,8 @@ void sparse_matmul_batch(Ctx &ctx, size_t n_req, const spfhe_matmul_req *reqs, C
 struct Server {
     Ctx &ctx;
     uint64_t budget;
-    uint64_t in_use = 0;
+    uint64_t in_use = 0;       // footprints of admitted, unfinished requests
+    uint64_t ws_reserved = 0;  // the engine's batch buffers at the highest admitted level
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
@@ -96,15 +103,68 @@ struct Server {
     std::map<uint64_t, std::unique_ptr<Entry>> entries;   // guarded by mu
     std::deque<uint64_t> queue;      // submitted, not yet admitted
     uint64_t next_ticket = 1;
+    uint64_t retried = 0;            // requests re-run alone after a failed wave
+    std::set<uint64_t> poisoned;     // future tickets marked for fault injection
     std::thread worker;
 
     Server(Ctx &c, uint64_t b) : ctx(c), budget(b) { worker = std::thread([this] { loop(); }); }
 
+    // device memory a request adds while it runs: its result chunks and its
+    // mask (a private copy of the caller's, or the level's library mask if
+    // none exists yet); the shared batch buffers are reserved separately
     uint64_t footprint_of(const Job &j) const
     {
         const int ell = j.Ach.empty() || !j.Ach[0] ? ctx.L : j.Ach[0]->level;
         return (uint64_t)j.n_c * 2ull * (uint64_t)std::max(ell - 2, 1) * ctx.n * sizeof(u64) +
-               (j.mask0 ? (uint64_t)(ell - 1) * ctx.n * sizeof(u64) : 0);
+               job_mask_bytes(ctx, j);
+    }
+
+    static int level_of(const Ctx &c, const Job &j) { return j.Ach.empty() || !j.Ach[0] ? c.L : j.Ach[0]->level; }
+
+    void complete(Entry &e)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        e.t_done = now_ms();
+        e.done = true;
+        in_use -= e.footprint;
+        cv_done.notify_all();
+    }
+
+    // a failed wave: requests whose last task had completed keep their
+    // results; every other running request is run again alone in a fresh
+    // engine (its results reallocated and zeroed), so only a request that also
+    // fails alone is reported failed
+    void recover(std::vector<Entry *> &running)
+    {
+        cudaStreamSynchronize(ctx.stream);
+        cudaGetLastError();
+        std::vector<Entry *> redo;
+        for (Entry *e : running) {
+            if (e->job.finished && e->job.done_ev && cudaEventQuery(e->job.done_ev) == cudaSuccess)
+                complete(*e);
+            else
+                redo.push_back(e);
+        }
+        running.clear();
+        cudaGetLastError();
+        for (Entry *e : redo) {
+            release_job(ctx, e->job, true);
+            reset_job(e->job);
+            ++retried;
+            try {
+                Engine solo(ctx);
+                solo.add(&e->job);
+                solo.run_all();
+                SPFHE_CHECK_CUDA(cudaStreamSynchronize(ctx.stream));
+                complete(*e);
+            } catch (const Error &err) {
+                finish_failed(*e, err.code, err.what());
+            } catch (const std::exception &err) {
+                finish_failed(*e, SPFHE_EINVAL, err.what());
+            } catch (...) {
+                finish_failed(*e, SPFHE_EINVAL, "unknown error");
+            }
+        }
     }
 
     void loop()
@@ -112,14 +172,24 @@ struct Server {
         cudaSetDevice(ctx.device);
         std::unique_ptr<Engine> eng(new Engine(ctx));
         std::vector<Entry *> running;   // admitted, event not yet complete
+        int ws_level = 0;               // level the workspace reservation covers
         for (;;) {
             std::vector<Entry *> admit;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 while (!queue.empty()) {
                     Entry *e = entries.at(queue.front()).get();
-                    if (in_use + e->footprint > budget && !running.empty()) break;
+                    // computed here: only this thread touches the context
+                    // (its level masks) while the server lives
+                    e->footprint = footprint_of(e->job);
+                    const int lv = std::max(ws_level, level_of(ctx, e->job));
+                    const uint64_t ws = engine_workspace_bound(ctx, lv);
+                    // a request is admitted whatever its size when nothing else
+                    // runs (nothing else could free memory for it)
+                    if (in_use + ws + e->footprint > budget && !(running.empty() && admit.empty())) break;
                     in_use += e->footprint;
+                    ws_level = lv;
+                    ws_reserved = ws;
                     admit.push_back(e);
                     queue.pop_front();
                 }
@@ -138,31 +208,29 @@ struct Server {
                     finish_failed(*e, err.code, err.what());
                 } catch (const std::exception &err) {
                     finish_failed(*e, SPFHE_EINVAL, err.what());
+                } catch (...) {
+                    finish_failed(*e, SPFHE_EINVAL, "unknown error");
                 }
             }
-            bool worked = false;
+            bool worked = false, failed = false;
             try {
                 worked = eng->step();
-            } catch (const Error &err) {
-                // a failed wave poisons every running request; start a clean engine
-                cudaStreamSynchronize(ctx.stream);
-                for (Entry *e : running) finish_failed(*e, err.code, err.what());
-                running.clear();
+                eng->take_finished();
+            } catch (...) {
+                failed = true;
+            }
+            if (failed) {
+                recover(running);
                 eng.reset(new Engine(ctx));
                 continue;
             }
-            eng->take_finished();
             if (!worked && !running.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
             // completions
             for (size_t i = 0; i < running.size();) {
                 Entry *e = running[i];
                 if (e->job.finished && cudaEventQuery(e->job.done_ev) == cudaSuccess) {
-                    std::lock_guard<std::mutex> lk(mu);
-                    e->t_done = now_ms();
-                    e->done = true;
-                    in_use -= e->footprint;
+                    complete(*e);
                     running.erase(running.begin() + i);
-                    cv_done.notify_all();
                 } else {
                     ++i;
                 }
@@ -174,6 +242,8 @@ struct Server {
     {
         std::lock_guard<std::mutex> lk(mu);
         release_job(ctx, e.job, true);
+        if (e.job.done_ev) cudaEventDestroy(e.job.done_ev);
+        e.job.done_ev = nullptr;
         e.status = code;
         e.err = msg;
         e.t_done = now_ms();
@@ -237,10 +307,10 @@ spfhe_status spfhe_server_submit(spfhe_server *srv, const spfhe_matmul_req *req,
         Server &s = *srv->s;
         auto e = std::make_unique<Server::Entry>();
         job_from_req(e->job, *req, result_chunks(s.ctx, *req));
-        e->footprint = s.footprint_of(e->job);
         e->t_submit = now_ms();
         std::lock_guard<std::mutex> lk(s.mu);
         const uint64_t t = s.next_ticket++;
+        if (s.poisoned.erase(t)) e->job.inject_fault = true;
         s.entries[t] = std::move(e);
         s.queue.push_back(t);
         *ticket = t;
@@ -290,6 +360,45 @@ spfhe_status spfhe_server_wait(spfhe_server *srv, uint64_t ticket, spfhe_ct **C_
         if (e.job.done_ev) cudaEventDestroy(e.job.done_ev);
         release_job(s.ctx, e.job, false);
         s.entries.erase(it);
+        return SPFHE_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+spfhe_status spfhe_server_inject_fault(spfhe_server *srv, uint64_t ticket)
+{
+    try {
+        if (!srv) throw Error(SPFHE_EINVAL, "null argument");
+        Server &s = *srv->s;
+        std::lock_guard<std::mutex> lk(s.mu);
+        if (ticket >= s.next_ticket) {   // a request not submitted yet
+            s.poisoned.insert(ticket);
+            return SPFHE_OK;
+        }
+        auto it = s.entries.find(ticket);
+        if (it == s.entries.end()) throw Error(SPFHE_EINVAL, "unknown ticket");
+        if (std::find(s.queue.begin(), s.queue.end(), ticket) == s.queue.end())
+            throw Error(SPFHE_EINVAL, "request already admitted");
+        it->second->job.inject_fault = true;
+        return SPFHE_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+spfhe_status spfhe_server_info(spfhe_server *srv, uint64_t *workspace_reserved, uint64_t *in_use,
+                               uint64_t *retried)
+{
+    try {
+        if (!srv) throw Error(SPFHE_EINVAL, "null argument");
+        Server &s = *srv->s;
+        std::lock_guard<std::mutex> lk(s.mu);
+        if (workspace_reserved) *workspace_reserved = s.ws_reserved;
+        if (in_use) *in_use = s.in_use;
+        if (retried) *retried = s.retried;
         return SPFHE_OK;
     } catch (const Error &e) {
         set_last_error(e.what());

@@ -128,6 +128,17 @@ void release_job(Ctx &ctx, Job &job, bool free_results)
             }
 }
 
+void reset_job(Job &job)
+{
+    job.C.clear();
+    job.mask = nullptr;
+    job.own_mask = nullptr;
+    job.ell = 0;
+    job.tasks_left = 0;
+    job.st_matches = job.st_relin = job.st_align = job.st_final = job.st_rescales = job.st_launches = 0;
+    job.finished = false;
+}
+
 struct Stats {
     uint64_t matches = 0, ks_relin = 0, ks_align = 0, ks_final = 0, rescales = 0;
 };

@@ -73,6 +73,8 @@ _SIGS = [
     ("spfhe_prof_read", ctypes.c_int, [handle, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), c_dblp, c_dblp, c_dblp]),
     ("spfhe_prof_classes", ctypes.c_int, []),
     ("spfhe_prof_keyswitch", ctypes.c_int, [handle, ctypes.POINTER(ctypes.c_uint64), c_dblp]),
+    ("spfhe_prof_transform_limbs", ctypes.c_int, [handle, ctypes.c_int, c_dblp, c_dblp, c_dblp]),
+    ("spfhe_prof_alu_rates", ctypes.c_int, [handle, c_dblp, ctypes.c_size_t]),
     ("spfhe_prof_class_name", ctypes.c_char_p, [ctypes.c_int]),
     ("spfhe_prof_alu_peak", ctypes.c_int, [handle, c_dblp, c_dblp, c_dblp, c_dblp]),
     ("spfhe_keygen", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle)]),
@@ -145,6 +147,9 @@ _SIGS += [
     ("spfhe_server_wait", ctypes.c_int, [handle, ctypes.c_uint64, ctypes.POINTER(handle), ctypes.c_size_t,
                                          ctypes.POINTER(Stats), c_dblp]),
     ("spfhe_server_destroy", ctypes.c_int, [handle]),
+    ("spfhe_server_inject_fault", ctypes.c_int, [handle, ctypes.c_uint64]),
+    ("spfhe_server_info", ctypes.c_int, [handle, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
     ("spfhe_tune_rotation_base", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                 ctypes.POINTER(SparseMeta), ctypes.POINTER(SparseMeta),
                                                 ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
@@ -284,6 +289,14 @@ def spfhe_prof_read(ctx, cls: int) -> dict:
     return {"launches": int(la.value), "ms": ms.value, "bytes": by.value, "work": wk.value}
 
 
+def spfhe_prof_transform_limbs(ctx, cls: int):
+    """(first-pass limbs, second-pass limbs, fused second-pass limbs) of a
+    transform class since spfhe_prof_enable."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().spfhe_prof_transform_limbs(ctx, cls, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def spfhe_prof_keyswitch(ctx):
     calls = ctypes.c_uint64()
     by = ctypes.c_double()
@@ -299,8 +312,21 @@ def spfhe_prof_alu_peak(ctx):
     return b.value, bs.value, i.value, w.value
 
 
+def spfhe_prof_alu_rates(ctx):
+    """(butterflies/s with mul_shoup3, mul_shoup3s, mul_shoup4s; mad.lo,
+    mad.wide, mad.hi per second) measured on the GPU."""
+    r = (ctypes.c_double * 6)()
+    _check(lib().spfhe_prof_alu_rates(ctx, r, 6))
+    return tuple(r)
+
+
 def spfhe_prof_all(ctx) -> dict:
-    return {spfhe_prof_class_name(c): spfhe_prof_read(ctx, c) for c in range(spfhe_prof_classes())}
+    out = {}
+    for c in range(spfhe_prof_classes()):
+        d = spfhe_prof_read(ctx, c)
+        d["limbs"] = spfhe_prof_transform_limbs(ctx, c)
+        out[spfhe_prof_class_name(c)] = d
+    return out
 
 
 def spfhe_keygen(ctx, seed: int):
@@ -556,6 +582,18 @@ def spfhe_tune_rotation_base(log_n: int, L: int, K: int, dnum: int, A: SparseMet
 
 def spfhe_server_destroy(srv):
     _check(lib().spfhe_server_destroy(srv))
+
+
+def spfhe_server_inject_fault(srv, ticket: int):
+    _check(lib().spfhe_server_inject_fault(srv, int(ticket)))
+
+
+def spfhe_server_info(srv):
+    """(bytes reserved for the shared batch buffers, bytes held by admitted
+    unfinished requests, requests re-run alone after a failed wave)"""
+    ws, used, retried = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().spfhe_server_info(srv, ctypes.byref(ws), ctypes.byref(used), ctypes.byref(retried)))
+    return int(ws.value), int(used.value), int(retried.value)
 
 
 def spfhe_sparse_matmul_ct_pt(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta, B_values, B_pts, n_c: int):

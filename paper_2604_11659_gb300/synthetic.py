@@ -155,15 +155,16 @@ def ring_serving() -> RingRecipe:
     return RingRecipe(log_n=16, q_bits=[60] + [45] * 30, dnum=4, scale_bits=45, k_stated=0, rot_base=16)
 
 
-def batch64_cases(seed: int = 2, count: int = 64, dims=(32, 64, 128, 256)) -> list:
+def batch64_cases(seed: int = 2, count: int = 64, dims=(32, 64, 128, 256), sparsity=(0.70, 0.95)) -> list:
     """`count` independent square products: d drawn from `dims` (the batch
-    workload uses {32, 64, 128, 256}), sparsity uniform in [0.70, 0.95], half
-    i.i.d. Bernoulli, half 2:4 structured."""
+    workload uses {32, 64, 128, 256}), sparsity uniform in `sparsity` (the
+    batch workload: [0.70, 0.95]), half i.i.d. Bernoulli, half 2:4
+    structured."""
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
         d = int(rng.choice(list(dims)))
-        s = float(rng.uniform(0.70, 0.95))
+        s = float(rng.uniform(sparsity[0], sparsity[1]))
         if b % 2 == 0:
             A = bernoulli_sparse(rng, d, d, s)
             B = bernoulli_sparse(rng, d, d, s)

@@ -41,13 +41,14 @@ def fake_library():
     sp = types.SimpleNamespace()
     sp.SpfheError = SpfheError
     sp.launches = 0
-    sp.spfhe_prof_alu_peak = lambda ctx: (1.1e12, 1.2e12, 2.0e13, 7.2e12)
+    sp.spfhe_prof_alu_rates = lambda ctx: (1.1e12, 1.2e12, 1.15e12, 2.0e13, 7.2e12, 1.1e13)
     sp.spfhe_prof_enable = lambda ctx, on: None
     sp.spfhe_launch_count = lambda ctx: sp.launches
 
     def prof_all(ctx):
         d = {c: {"launches": 0, "ms": 0.0, "bytes": 0.0, "work": 0.0} for c in CLASSES}
-        d["ks_ntt_fwd"] = {"launches": 100, "ms": 600.0, "bytes": 2.0e12, "work": 4.0e11}
+        d["ks_ntt_fwd"] = {"launches": 100, "ms": 600.0, "bytes": 2.0e12, "work": 4.0e11,
+                           "limbs": (400.0, 250.0, 150.0)}
         d["modup_bconv"] = {"launches": 50, "ms": 200.0, "bytes": 3.0e11, "work": 1.0e11}
         d["ks_inner_product"] = {"launches": 50, "ms": 100.0, "bytes": 5.0e11, "work": 0.0}
         return d
@@ -161,16 +162,17 @@ def test_default_line_carries_the_contract(stubbed, monkeypatch, capsys):
                                      "tuner_key_gib": pytest.approx(37251710976 / 2 ** 30)}
     assert line["graph"]["vs_eager"] == pytest.approx(1.0)
     assert line["variant_grouped"]["ks_per_step"] == 11403 + 3003 + 11423
-    for k in ("batch", "serve", "dense_layer_ct_pt"):
+    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt"):
         assert k in line
 
 
 def test_skips_leave_their_keys_out(stubbed, monkeypatch, capsys):
     line = _run(monkeypatch, capsys, ["--steps", "1", "--warmup", "3", "--graph-steps", "0", "--grouped-steps", "0",
-                                      "--batch-products", "0", "--serve-requests", "0", "--dense-layer", "0",
+                                      "--batch-products", "0", "--batch128-products", "0", "--serve-requests", "0",
+                                      "--dense-layer", "0",
                                       "--no-cpu-baseline"])
     assert line["graph"] is None and line["variant_grouped"] is None
-    for k in ("batch", "serve", "dense_layer_ct_pt", "cpu_baseline"):
+    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "cpu_baseline"):
         assert k not in line
     assert line["ms_per_step"] == pytest.approx(STEP_MS)
 

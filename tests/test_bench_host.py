@@ -3,33 +3,29 @@ the key-switching forward transforms recovers the pass mix it is built from."""
 import bench
 
 
-def test_ks_ntt_fwd_traffic_recovers_pass_mix():
-    n, log_n = 1 << 16, 16
+def test_ks_ntt_fwd_traffic_weights_pass_kinds():
+    """Per-launch DRAM traffic = the limbs of each pass kind times that kind's
+    measured bytes per limb, over the class's launches."""
     la, lb, lf = 120.0, 70.0, 50.0          # pass-A, plain pass-B, fused pass-B limbs
-    work = 0.5 * n * 8 * la + 0.5 * n * 8 * (lb + lf)
-    nbytes = 16.0 * n * (la + lb) + 40.0 * n * lf
-    launches = 6
     d = bench.NTT_FWD_DRAM_PER_LIMB
-    want = (la * d["a"] + lb * d["b"] + lf * d["b_moddown"]) / launches
-    got = bench.ks_ntt_fwd_traffic(work, nbytes, launches, n, log_n)
-    assert abs(got - want) < 1e-6 * want
+    want = (la * d["a"] + lb * d["b"] + lf * d["b_moddown"]) / 6
+    assert abs(bench.ks_ntt_fwd_traffic((la, lb, lf), 6) - want) < 1e-6 * want
+    assert bench.ks_ntt_fwd_traffic((64.0, 64.0, 0.0), 2) == (64 * d["a"] + 64 * d["b"]) / 2
 
 
-def test_ks_ntt_fwd_traffic_without_fused_passes():
-    n, log_n = 1 << 16, 16
-    la = 64.0
-    work = 0.5 * n * log_n * la
-    got = bench.ks_ntt_fwd_traffic(work, 32.0 * n * la, 2, n, log_n)
-    d = bench.NTT_FWD_DRAM_PER_LIMB
-    assert abs(got - la * (d["a"] + d["b"]) / 2) < 1e-6 * got
+def test_both_arms_share_the_config():
+    c = bench.bench_config("w")
+    assert c == bench.bench_config("w") and set(c) == {"workload", "l2", "parallelism"}
 
 
 def test_alu_microbench_summary():
-    meas = (1.5e12, 1.2e12, 2.0e13, 1.0e13)
+    meas = (1.5e12, 1.2e12, 1.4e12, 2.0e13, 1.0e13, 1.2e13)
     out = bench.alu_microbench(meas, 0.75e12, 2070.0)
     assert out["frac_of_butterfly_peak"] == 0.5
-    assert bench.alu_microbench((1.0e12, 1.5e12, 2.0e13, 1.0e13), 0.75e12, 2070.0)["frac_of_butterfly_peak"] == 0.5
+    meas2 = (1.0e12, 1.2e12, 1.5e12, 2.0e13, 1.0e13, 1.2e13)
+    assert bench.alu_microbench(meas2, 0.75e12, 2070.0)["frac_of_butterfly_peak"] == 0.5
     assert abs(out["imad_per_clk_per_sm"] - 2.0e13 / (152 * 2070e6)) < 1e-9
+    assert abs(out["imad_hi_per_clk_per_sm"] - 1.2e13 / (152 * 2070e6)) < 1e-9
     assert bench.alu_microbench(None, 1.0, 2070.0) is None
     assert "frac_of_butterfly_peak" not in bench.alu_microbench(meas, None, 2070.0)
 

@@ -185,3 +185,59 @@ def test_graph_batch_errors(setup):
     hs, _ = sp.spfhe_sparse_matmul_ct_ct(p.ctx, p.gkeys, r.Am, r.gA, r.Bm, r.gB, r.gmask, r.n_c)
     for h, a in zip(hs, r.alone):
         assert np.array_equal(p.export_ct(p.track("ct", h)), a)
+
+
+def test_server_isolates_a_failed_wave(setup):
+    """A host-side injected failure in the waves of one request (no GPU fault:
+    the engine raises SPFHE_ECUDA before launching that wave) fails only that
+    request: the others, mixed into the same waves, are run again alone and
+    return exactly the bits of their single calls; the server keeps serving
+    requests submitted afterwards."""
+    p = setup
+    sp = p.spfhe
+    srv = sp.spfhe_server_create(p.ctx, 1 << 30)
+    try:
+        sp.spfhe_server_inject_fault(srv, 2)   # the second request submitted
+        tickets = [sp.spfhe_server_submit(srv, _req(p, r)) for r in p.reqs]
+        assert tickets[1] == 2
+        for i, (r, t) in enumerate(zip(p.reqs, tickets)):
+            if i == 1:
+                with pytest.raises(sp.SpfheError) as e:
+                    sp.spfhe_server_wait(srv, t, r.n_c)
+                assert e.value.status == -6 and "injected" in str(e.value)
+                continue
+            hs, st, lat = sp.spfhe_server_wait(srv, t, r.n_c)
+            assert st["matches"] == r.stats["matches"]
+            for h, a in zip(hs, r.alone):
+                assert np.array_equal(p.export_ct(p.track("ct", h)), a)
+        ws, in_use, retried = sp.spfhe_server_info(srv)
+        assert retried >= 1 and in_use == 0 and ws > 0
+        # a later request runs normally
+        r = p.reqs[1]
+        t = sp.spfhe_server_submit(srv, _req(p, r))
+        hs, st, _ = sp.spfhe_server_wait(srv, t, r.n_c)
+        for h, a in zip(hs, r.alone):
+            assert np.array_equal(p.export_ct(p.track("ct", h)), a)
+        with pytest.raises(sp.SpfheError):
+            sp.spfhe_server_inject_fault(srv, t)   # already finished: unknown
+    finally:
+        sp.spfhe_server_destroy(srv)
+
+
+def test_server_admission_budget_serialises(setup):
+    """A budget below the shared batch buffers plus two requests admits one
+    request at a time (each still admitted when nothing else runs); results
+    stay bit-identical to the single calls."""
+    p = setup
+    sp = p.spfhe
+    srv = sp.spfhe_server_create(p.ctx, 1)
+    try:
+        tickets = [sp.spfhe_server_submit(srv, _req(p, r)) for r in p.reqs]
+        for r, t in zip(p.reqs, tickets):
+            hs, st, _ = sp.spfhe_server_wait(srv, t, r.n_c)
+            for h, a in zip(hs, r.alone):
+                assert np.array_equal(p.export_ct(p.track("ct", h)), a)
+        ws, in_use, retried = sp.spfhe_server_info(srv)
+        assert in_use == 0 and retried == 0 and ws > 0
+    finally:
+        sp.spfhe_server_destroy(srv)

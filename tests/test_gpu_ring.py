@@ -37,11 +37,13 @@ def test_moduli_match_oracle(pair):
 @pytest.mark.parametrize("log_n,q_bits,split", [(2, [60, 40, 40], 0), (4, [60, 40, 40], 0), (10, [60, 45, 45], 0),
                                                 (12, [60, 40, 40, 40], 0), (16, [60, 45, 45], 0),
                                                 (16, [60, 45, 59, 57], 7), (16, [60, 45, 45], 9),
-                                                (17, [60, 50, 50], 0), (17, [60, 50, 50], 9)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+                                                (17, [60, 50, 50], 0), (17, [60, 50, 50], 9),
+                                                (16, [60, 58, 56, 45], 0), (17, [60, 57, 58], 9)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_ntt_forward_inverse_bit_exact(log_n, q_bits, split, variant):
-    """Both butterfly paths (reduction-free below 2^58, bounded at and above),
-    every pass split and kernel variant, against the oracle's transform."""
+    """Both butterfly paths (reduction-free below 2^58, or 2^57 for variant 5,
+    bounded at and above), every pass split and kernel variant, against the
+    oracle's transform; limb 1 holds q - 1 everywhere (the largest inputs)."""
     sp = need_gpu()
     import torch
     if variant and log_n < 12:
@@ -55,6 +57,7 @@ def test_ntt_forward_inverse_bit_exact(log_n, q_bits, split, variant):
         rng = np.random.default_rng(log_n)
         x = np.stack([rng.integers(0, m, n, dtype=np.uint64) for m in p.P.mods])
         x[0, :3] = [0, p.P.mods[0] - 1, 1]
+        x[1, :] = p.P.mods[1] - 1
         mi = np.arange(M, dtype=np.int32)
         want = p.o.rns_ntt(x, mi)
         t = torch.from_numpy(x.view(np.int64)).cuda()

@@ -487,6 +487,152 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(5, 0, 0), sparsity=(0.70, 0
     return out
 
 
+def naive_sweep(stream, sparsities=(0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0), seed=0, reps=2):
+    """The comparison of Sec. 4 / Fig. 4a on the 16x16 workload's ring
+    (N=2^12, L=4, dnum=1): CSR/C (Alg. 1 + Alg. 2) against Naive Sparse
+    (element-wise, a product skipped when either value is zero) and Naive
+    Dense (every product) over sparsity 0-100 %, 16x16 operands of the 16x16
+    recipe at each sparsity.  Times are CUDA-event means over `reps` runs after
+    one warm-up run; every result is decrypted and compared with FP64."""
+    import torch
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    rec = synthetic.ring_small_16x16()
+    ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    keys = sp.spfhe_keygen(ctx, 123)
+    S = (1 << rec.log_n) // 2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def enc(vals, s0):
+        out = []
+        for c in range(max(1, -(-len(vals) // S))):
+            z = np.zeros(S)
+            part = vals[c * S:(c + 1) * S]
+            z[: len(part)] = part
+            pt = sp.spfhe_encode(ctx, z, rec.L, rec.scale)
+            out.append(sp.spfhe_encrypt(ctx, keys, pt, s0 + c))
+            sp.spfhe_pt_free(pt)
+        return out
+
+    rows = []
+    for si, s in enumerate(sparsities):
+        case = synthetic.case_16x16(seed=seed + si, sparsity=s)
+        A, B = case.A, case.B
+        Aip, Aix, Ad = to_csr(A)
+        Bip, Bix, Bd = to_csr(B.T)
+        Am = sp.sparse_meta(Aip, Aix, 16, 16)
+        Bm = sp.sparse_meta(Bip, Bix, 16, 16)
+        a_sp, b_sp = enc(Ad, 10), enc(Bd, 20)
+        a_dn, b_dn = enc(A.reshape(-1), 30), enc(B.reshape(-1), 40)
+        arms = {"csr_c": lambda: sp.spfhe_sparse_matmul_ct_ct(ctx, keys, Am, a_sp, Bm, b_sp, None, 1),
+                "naive_sparse": lambda: sp.spfhe_naive_matmul_ct_ct(ctx, keys, sp.NAIVE_SPARSE, A != 0, B != 0,
+                                                                   a_dn, b_dn, None, 1),
+                "naive_dense": lambda: sp.spfhe_naive_matmul_ct_ct(ctx, keys, sp.NAIVE_DENSE, A != 0, B != 0,
+                                                                  a_dn, b_dn, None, 1)}
+        row = {"sparsity": s}
+        for name, fn in arms.items():
+            outs, st = fn()
+            for h in outs:
+                sp.spfhe_ct_free(h)
+            torch.cuda.synchronize()
+            ev0.record()
+            for r in range(reps):
+                outs, st = fn()
+                if r < reps - 1:
+                    for h in outs:
+                        sp.spfhe_ct_free(h)
+            ev1.record()
+            torch.cuda.synchronize()
+            C = decrypt_matrix(sp, ctx, keys, outs, 16, 16, S)
+            for h in outs:
+                sp.spfhe_ct_free(h)
+            row[name] = {"ms": ev0.elapsed_time(ev1) / reps, "products": st["matches"],
+                         "key_switches": st["ks_relin"] + st["ks_align"] + st["ks_final"],
+                         "max_abs_err": float(np.max(np.abs(C - A @ B)))}
+        for h in a_sp + b_sp + a_dn + b_dn:
+            sp.spfhe_ct_free(h)
+        rows.append(row)
+    sp.spfhe_keys_free(keys)
+    sp.spfhe_ctx_destroy(ctx)
+    return {"workload": "16x16 x 16x16 at sparsity 0-100 %, N=2^12, L=4, dnum=1, rotation base 16 (Sec. 4 / Fig. 4a)",
+            "methods": {"csr_c": "Alg. 1 + Alg. 2 (CSR x CSC packing, one operand rotated per match)",
+                        "naive_sparse": "element-wise over dense packing, a product skipped when either value is zero",
+                        "naive_dense": "element-wise over dense packing, every product"},
+            "reps": reps, "warmup": 1, "rows": rows}
+
+
+def workload_16x16_end_to_end(stream, seed=0, reps=5):
+    """The 16x16 workload end to end on both sides: the library's Alg. 1 +
+    Alg. 2 product (CUDA events, mean of `reps` after one warm-up; Sec. 4
+    averages five runs and leaves conversion, encoding and encryption out) and
+    the plain CPU oracle's full, unprojected Alg. 1 + Alg. 2 on the same
+    workload (host cores, one run), each with its error against FP64."""
+    import torch
+    from oracle import build as obuild
+    obuild.build()
+    from oracle import ckks, spmspm
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    case = synthetic.case_16x16(seed=seed)
+    rec = case.ring
+    ctx = sp.spfhe_ctx_create(gparams.ctx_params(rec, rot_base=16), stream)
+    keys = sp.spfhe_keygen(ctx, 5)
+    S = (1 << rec.log_n) // 2
+    Aip, Aix, Ad = to_csr(case.A)
+    Bip, Bix, Bd = to_csr(case.B.T)
+    Am, Bm = sp.sparse_meta(Aip, Aix, 16, 16), sp.sparse_meta(Bip, Bix, 16, 16)
+    cts = []
+    for vals, s0 in ((Ad, 1), (Bd, 2)):
+        z = np.zeros(S)
+        z[: len(vals)] = vals
+        pt = sp.spfhe_encode(ctx, z, rec.L, rec.scale)
+        cts.append(sp.spfhe_encrypt(ctx, keys, pt, s0))
+        sp.spfhe_pt_free(pt)
+    outs, st = sp.spfhe_sparse_matmul_ct_ct(ctx, keys, Am, [cts[0]], Bm, [cts[1]], None, 1)
+    for h in outs:
+        sp.spfhe_ct_free(h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for r in range(reps):
+        outs, st = sp.spfhe_sparse_matmul_ct_ct(ctx, keys, Am, [cts[0]], Bm, [cts[1]], None, 1)
+        if r < reps - 1:
+            for h in outs:
+                sp.spfhe_ct_free(h)
+    ev1.record()
+    torch.cuda.synchronize()
+    gpu_ms = ev0.elapsed_time(ev1) / reps
+    C = decrypt_matrix(sp, ctx, keys, outs, 16, 16, S)
+    gpu_err = float(np.max(np.abs(C - case.A @ case.B)))
+    for h in outs + cts:
+        sp.spfhe_ct_free(h)
+    sp.spfhe_keys_free(keys)
+    sp.spfhe_ctx_destroy(ctx)
+    # the oracle, the whole product (keys and encryption outside the timing)
+    cores = ckks.threads(os.cpu_count() or 1)
+    K = ckks.special_prime_count(rec.q_bits, rec.dnum, rec.p_bits, rec.k_stated)
+    P = ckks.make_params(rec.log_n, rec.q_bits, K, rec.dnum, rec.scale, rot_base=16)
+    o = ckks.Oracle(P)
+    Acsr, Bcsc = spmspm.dense_to_csr(case.A), spmspm.dense_to_csc(case.B)
+    amts = set()
+    for a in spmspm.final_rotation_amounts(Acsr[:2], Bcsc[:2], 16, 16, P.slots):
+        amts.update(ckks.rotation_plan(a, P.slots, 16))
+    okeys = o.keygen(6, rot_amounts=sorted(amts))
+    rng = np.random.default_rng(7)
+    A_ct = [o.encrypt(o.encode(z, P.L, P.scale), okeys, rng) for z in spmspm.pack_values(Acsr[2], P.slots)]
+    B_ct = [o.encrypt(o.encode(z, P.L, P.scale), okeys, rng) for z in spmspm.pack_values(Bcsc[2], P.slots)]
+    t0 = time.perf_counter()
+    res = spmspm.spmspm_ct_ct(o, okeys, Acsr[:2], A_ct, Bcsc[:2], B_ct, 16, 16)
+    oracle_s = time.perf_counter() - t0
+    oerr = float(np.max(np.abs(spmspm.decrypt_result(o, okeys, res, 16, 16) - case.A @ case.B)))
+    return {"workload": "16x16 ct x ct, 75%% sparsity, N=2^12, L=4, dnum=1, K=%d, rotation base 16" % K,
+            "matches": st["matches"], "gpu_ms": gpu_ms, "gpu_reps": reps, "gpu_max_abs_err": gpu_err,
+            "oracle_s": oracle_s, "oracle_cores": cores, "oracle_max_abs_err": oerr,
+            "oracle": "full Alg. 1 + Alg. 2, not projected (one run)"}
+
+
 def dense_layer_pt(stream, rot_base=16):
     """The pruned dense layer at the paper's sizing (N=2^17, L=35, dnum=5,
     K=6): encrypted 64x784 ReLU-like activations times plaintext 784x128
@@ -811,6 +957,8 @@ def main():
                     help="timed launches of the headline product captured as one CUDA graph (0: skip)")
     ap.add_argument("--dense-layer", type=int, default=1,
                     help="1: run the N=2^17 dense-layer ct x pt product once (lazy accumulation)")
+    ap.add_argument("--naive-sweep", type=int, default=1,
+                    help="1: CSR/C vs Naive Sparse vs Naive Dense over sparsity 0-100 %% at 16x16 (Fig. 4a)")
     ap.add_argument("--grouped-steps", type=int, default=2,
                     help="timed steps of the lazy-accumulation variant (0: skip)")
     ap.add_argument("--ntt-chunk", type=int, default=-1,
@@ -1057,6 +1205,10 @@ def main():
         line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
     if args.dense_layer:
         line["dense_layer_ct_pt"] = dense_layer_pt(stream)
+    if args.naive_sweep:
+        line["naive_sweep_16x16"] = naive_sweep(stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["workload_16x16"] = workload_16x16_end_to_end(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(case, args.rot_base)
     if rank == 0:

@@ -355,6 +355,32 @@ spfhe_status spfhe_sparse_matmul_ct_ct(spfhe_ctx *ctx, const spfhe_keys *keys,
                                        const spfhe_pt *mask0, spfhe_ct **C_chunks, size_t n_c,
                                        spfhe_stats *stats);
 
+/* ---- the paper's element-wise baselines (Sec. 4) ------------------------ */
+/* Naive Dense multiplies every element pair individually; Naive Sparse is
+ * element-wise too but skips pairs by the zero pattern (the paper's prior
+ * method).  SPFHE_NAIVE_SPARSE skips a pair when either value is zero (the
+ * exact product with the fewest products: the pairs Alg. 1 matches);
+ * SPFHE_NAIVE_SPARSE_LITERAL skips it only when both are zero, as printed. */
+typedef enum { SPFHE_NAIVE_DENSE = 0, SPFHE_NAIVE_SPARSE = 1, SPFHE_NAIVE_SPARSE_LITERAL = 2 } spfhe_naive_mode;
+/* C = A B through an element-wise baseline over densely packed operands:
+ * A (rows x inner) row-major, element (i, k) in slot (i*inner + k) mod S of
+ * chunk (i*inner + k) / S, n_a = ceil(rows*inner / S) ciphertexts; B (inner x
+ * cols) row-major the same way, n_b = ceil(inner*cols / S).  A_nonzero /
+ * B_nonzero: host arrays of rows*inner / inner*cols bytes, nonzero where the
+ * element is nonzero (plaintext structure, like the CSR/CSC metadata of the
+ * sparse product; read during the call only).  For every pair (i, j, k) the
+ * mode keeps, in the order i, j, k, both ciphertexts are rotated so the two
+ * elements sit in slot 0 (one rotation per operand, none when already
+ * there), then Alg. 2's chain runs with the mask at slot 0 and the final
+ * rotation to t = i*cols + j.  mask0, C_chunks (n_c = ceil(rows*cols / S)),
+ * levels, scales and errors as in spfhe_sparse_matmul_ct_ct; stats.matches
+ * counts the pairs computed. */
+spfhe_status spfhe_naive_matmul_ct_ct(spfhe_ctx *ctx, const spfhe_keys *keys, int mode, int32_t rows,
+                                      int32_t inner, int32_t cols, const uint8_t *A_nonzero,
+                                      const uint8_t *B_nonzero, spfhe_ct *const *A_chunks, size_t n_a,
+                                      spfhe_ct *const *B_chunks, size_t n_b, const spfhe_pt *mask0,
+                                      spfhe_ct **C_chunks, size_t n_c, spfhe_stats *stats);
+
 /* C = A B with A encrypted (packed as above) and B a plaintext (CSC).  Per
  * match the weight plaintext encodes B[k,j] in A's slot at scale q_{L-1}
  * (alignment of B becomes re-encoding, the mask merges into it), then

@@ -525,3 +525,100 @@ def final_rotation_amounts(A_csr, B_csc, rows: int, cols: int, slots: int) -> li
             amts.add(abs(sa - sb))
         amts.add((min(sa, sb) - (mt.i * cols + mt.j) % slots) % slots)
     return sorted(amts)
+
+
+# ---------------------------------------------------------------------------
+# the paper's element-wise baselines (Sec. 4): Naive Dense and Naive Sparse
+# ---------------------------------------------------------------------------
+NAIVE_DENSE, NAIVE_SPARSE, NAIVE_SPARSE_LITERAL = 0, 1, 2
+
+
+def dense_pack(M: np.ndarray, slots: int) -> list:
+    """Reading R16: a dense operand packed row-major, element (r, c) of an
+    R x C matrix in slot (r C + c) mod S of chunk (r C + c) // S (zeros
+    included)."""
+    return pack_values(np.asarray(M, dtype=np.float64).reshape(-1), slots)
+
+
+def naive_triples(A_nz: np.ndarray, B_nz: np.ndarray, mode: int) -> list:
+    """The (i, j, k) products an element-wise method computes, in the order
+    i, j, k (every element multiplied individually, Sec. 4):
+      NAIVE_DENSE: all of them;
+      NAIVE_SPARSE: those with A[i, k] and B[k, j] both nonzero (reading G15:
+        skipping a product when either value is zero, which still gives the
+        exact product);
+      NAIVE_SPARSE_LITERAL: those with at least one of the two nonzero (the
+        printed rule: skip only where both values are zero)."""
+    rows, inner = A_nz.shape
+    cols = B_nz.shape[1]
+    out = []
+    for i in range(rows):
+        for j in range(cols):
+            for k in range(inner):
+                a, b = bool(A_nz[i, k]), bool(B_nz[k, j])
+                if mode == NAIVE_SPARSE and not (a and b):
+                    continue
+                if mode == NAIVE_SPARSE_LITERAL and not (a or b):
+                    continue
+                out.append((i, j, k))
+    return out
+
+
+def naive_ct_ct(orc: Oracle, keys: Keys, A_cts: list, B_cts: list, A_nz: np.ndarray, B_nz: np.ndarray,
+                mode: int, mask_pt: Pt | None = None, counts: OpCounts | None = None) -> list:
+    """The element-wise baselines of Sec. 4 over densely packed encrypted
+    operands (reading R16): for every product (i, j, k) that `mode` keeps,
+    both ciphertexts are rotated so that A[i, k] and B[k, j] sit in slot 0
+    (the naive alignment: one rotation per operand, none when the element is
+    already there), multiplied and relinearised, rescaled, masked to slot 0,
+    rescaled, rotated to the target slot t = i cols + j and added into the
+    result chunk t // S; the chain after the alignment is Alg. 2's.
+    A_nz, B_nz: the zero patterns (plaintext structure, like CSR metadata).
+    Result chunks at level ell - 2, R3 layout."""
+    P = orc.P
+    S = P.slots
+    if counts is None:
+        counts = OpCounts()
+    rows, inner = A_nz.shape
+    cols = B_nz.shape[1]
+    nres = max(1, -(-(rows * cols) // S))
+    ell = A_cts[0].level
+    result = [orc.zero_ct(ell - 2, result_scale(orc, ell, A_cts[0].scale, B_cts[0].scale)) for _ in range(nres)]
+    mask = make_mask(orc, 0, ell - 1) if mask_pt is None else mask_pt
+    for i, j, k in naive_triples(A_nz, B_nz, mode):
+        counts.matches += 1
+        ca, sa = divmod(i * inner + k, S)
+        cb, sb = divmod(k * cols + j, S)
+        vA, vB = A_cts[ca], B_cts[cb]
+        if sa:
+            vA = orc.rotate(vA, sa, keys)
+            counts.ks_align += len(rotation_plan(sa, S, P.rot_base))
+        if sb:
+            vB = orc.rotate(vB, sb, keys)
+            counts.ks_align += len(rotation_plan(sb, S, P.rot_base))
+        dot = orc.mult_relin(vA, vB, keys)
+        counts.ks_relin += 1
+        dot = orc.rescale(dot)
+        dot = orc.mul_plain(dot, mask)
+        dot = orc.rescale(dot)
+        counts.rescales += 2
+        t = i * cols + j
+        rc, ts = divmod(t, S)
+        r = (-ts) % S
+        counts.ks_final += len(rotation_plan(r, S, P.rot_base))
+        dot = orc.rotate(dot, r, keys)
+        result[rc] = orc.add(result[rc], dot)
+    return result
+
+
+def naive_rotation_amounts(rows: int, inner: int, cols: int, slots: int) -> list:
+    """Every rotation amount the element-wise baselines may request."""
+    amts = set()
+    for p in range(rows * inner):
+        amts.add(p % slots)
+    for p in range(inner * cols):
+        amts.add(p % slots)
+    for t in range(rows * cols):
+        amts.add((-(t % slots)) % slots)
+    amts.discard(0)
+    return sorted(amts)

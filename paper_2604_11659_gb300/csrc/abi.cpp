@@ -621,6 +621,24 @@ spfhe_status spfhe_sparse_matmul_ct_ct(spfhe_ctx *ctx, const spfhe_keys *keys, c
     });
 }
 
+spfhe_status spfhe_naive_matmul_ct_ct(spfhe_ctx *ctx, const spfhe_keys *keys, int mode, int32_t rows,
+                                      int32_t inner, int32_t cols, const uint8_t *A_nonzero,
+                                      const uint8_t *B_nonzero, spfhe_ct *const *A_chunks, size_t n_a,
+                                      spfhe_ct *const *B_chunks, size_t n_b, const spfhe_pt *mask0,
+                                      spfhe_ct **C_chunks, size_t n_c, spfhe_stats *stats)
+{
+    return guard([&] {
+        need(keys && A_chunks && B_chunks && C_chunks, "null argument");
+        Ctx &c = C(ctx);
+        std::vector<Ct *> a(n_a), b(n_b), out(n_c, nullptr);
+        for (size_t i = 0; i < n_a; ++i) a[i] = A_chunks[i] ? A_chunks[i]->c : nullptr;
+        for (size_t i = 0; i < n_b; ++i) b[i] = B_chunks[i] ? B_chunks[i]->c : nullptr;
+        naive_ct_ct(c, *keys->k, mode, rows, inner, cols, A_nonzero, B_nonzero, a.data(), n_a, b.data(), n_b,
+                    mask0 ? mask0->p : nullptr, out.data(), n_c, stats);
+        for (size_t i = 0; i < n_c; ++i) C_chunks[i] = wrap(out[i]);
+    });
+}
+
 spfhe_status spfhe_sparse_matmul_ct_ct_grouped(spfhe_ctx *ctx, const spfhe_keys *keys, const spfhe_sparse_meta *A_csr,
                                                spfhe_ct *const *A_chunks, size_t n_a, const spfhe_sparse_meta *B_csc,
                                                spfhe_ct *const *B_chunks, size_t n_b, const spfhe_pt *mask0,

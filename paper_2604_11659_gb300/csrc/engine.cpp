@@ -32,7 +32,7 @@ uint64_t engine_workspace_bound(const Ctx &ctx, int ell)
     const uint64_t B = (uint64_t)match_batch_size(ctx);
     const uint64_t l = (uint64_t)ell, K = (uint64_t)ctx.K;
     const uint64_t beta = (l + ctx.alpha - 1) / ctx.alpha;
-    const uint64_t limbs = 2 * l        // WS_ALIGN (G = B alignment outputs)
+    const uint64_t limbs = 2 * l        // WS_ALIGN (G + 1 = B + 1 alignment outputs)
                            + 3 * l      // WS_TENSOR
                            + 2 * l      // WS_RELIN_OUT
                            + 2 * l      // WS_LEVEL1 (2 (ell-1), rounded up)
@@ -45,7 +45,7 @@ uint64_t engine_workspace_bound(const Ctx &ctx, int ell)
                            + 2 * l      // WS_KS_CONV
                            + l          // WS_ROT_TMP
                            + 4 * l;     // WS_ROT_OUT_A, WS_ROT_OUT_B
-    return B * limbs * (uint64_t)ctx.n * sizeof(u64);
+    return (B * limbs + 2 * l) * (uint64_t)ctx.n * sizeof(u64);
 }
 
 uint64_t job_mask_bytes(const Ctx &ctx, const Job &job)
@@ -119,53 +119,119 @@ int check_ct_ct(const Ctx &ctx, const spfhe_sparse_meta &A, const std::vector<Ct
     return ell;
 }
 
+// checks shared by the ct x ct products on levels and scales; returns the
+// operands' level and their product's result scale
+static int check_levels_scales(const Ctx &ctx, const std::vector<Ct *> &Ach, const std::vector<Ct *> &Bch,
+                               double *rscale)
+{
+    if (Ach.empty() || Bch.empty()) throw Error(SPFHE_EINVAL, "no operand chunks");
+    const int ell = Ach[0] ? Ach[0]->level : 0;
+    for (Ct *c : Ach)
+        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "A chunks must share one level");
+    for (Ct *c : Bch)
+        if (!c || !c->d || c->level != ell) throw Error(SPFHE_ELEVEL, "B chunks must share A's level");
+    if (ell < 3) throw Error(SPFHE_ELEVEL, "ct x ct needs operands at level >= 3");
+    const double sa = Ach[0]->scale, sb = Bch[0]->scale;
+    for (Ct *c : Ach)
+        if (std::fabs(c->scale - sa) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A chunk scales differ");
+    for (Ct *c : Bch)
+        if (std::fabs(c->scale - sb) > 1e-9 * sb) throw Error(SPFHE_ESCALE, "B chunk scales differ");
+    if (std::fabs(sa - sb) > 1e-9 * sa) throw Error(SPFHE_ESCALE, "A and B scales differ");
+    *rscale = sa * sb / (double)ctx.mods[ell - 1];
+    return ell;
+}
+
 void Engine::add(Job *job)
 {
     Ctx &ctx = ctx_;
     const int S = ctx.S;
     const size_t n = ctx.n;
-    job->A.indptr = job->aip.data();
-    job->A.indices = job->aix.empty() ? nullptr : job->aix.data();
-    job->B.indptr = job->bip.data();
-    job->B.indices = job->bix.empty() ? nullptr : job->bix.data();
     if (!job->keys) throw Error(SPFHE_EINVAL, "null keys");
-    const int ell = check_ct_ct(ctx, job->A, job->Ach, job->B, job->Bch, job->n_c, &job->rscale);
-    job->ell = ell;
-    job->id = next_id_++;
-
-    const std::vector<MatchRec> ms = plan_alg1(job->A, job->B);
-    // keys first: nothing is allocated or launched for a job that would fail
-    if (!ms.empty() && !job->keys->relin) throw Error(SPFHE_EKEY, "no relinearisation key");
     struct Plan {
         int src_a, src_b, min_slot, rf, rc;
     };
-    std::vector<Plan> plan(ms.size());
-    std::map<std::tuple<int, int, int>, int> local_rot;
+    std::vector<Plan> plan;
+    // rotation tasks of this job: (operand, chunk, amount), and for the
+    // element-wise baselines the task rotating the other operand of the same
+    // product (-1: none)
     std::vector<std::tuple<int, int, int>> local_list;
-    auto rot_of = [&](int op, int chunk, int amt) {
-        auto key = std::make_tuple(op, chunk, amt);
-        auto it = local_rot.find(key);
-        if (it != local_rot.end()) return it->second;
-        const int id = (int)local_list.size();
-        local_rot[key] = id;
-        local_list.push_back(key);
-        return id;
-    };
-    for (size_t x = 0; x < ms.size(); ++x) {
-        const MatchRec &mt = ms[x];
-        const int ca = mt.a_pos / S, sa_ = mt.a_pos % S, cb = mt.b_pos / S, sb_ = mt.b_pos % S;
-        Plan p{-(ca + 1), -(cb + 1), sa_, 0, 0};
-        if (sa_ < sb_)
-            p.src_b = rot_of(1, cb, sb_ - sa_);
-        else if (sb_ < sa_) {
-            p.src_a = rot_of(0, ca, sa_ - sb_);
-            p.min_slot = sb_;
+    std::vector<int> partner;
+    int ell = 0;
+    if (job->naive < 0) {
+        job->A.indptr = job->aip.data();
+        job->A.indices = job->aix.empty() ? nullptr : job->aix.data();
+        job->B.indptr = job->bip.data();
+        job->B.indices = job->bix.empty() ? nullptr : job->bix.data();
+        ell = check_ct_ct(ctx, job->A, job->Ach, job->B, job->Bch, job->n_c, &job->rscale);
+        const std::vector<MatchRec> ms = plan_alg1(job->A, job->B);
+        std::map<std::tuple<int, int, int>, int> local_rot;
+        auto rot_of = [&](int op, int chunk, int amt) {
+            auto key = std::make_tuple(op, chunk, amt);
+            auto it = local_rot.find(key);
+            if (it != local_rot.end()) return it->second;
+            const int id = (int)local_list.size();
+            local_rot[key] = id;
+            local_list.push_back(key);
+            partner.push_back(-1);
+            return id;
+        };
+        plan.resize(ms.size());
+        for (size_t x = 0; x < ms.size(); ++x) {
+            const MatchRec &mt = ms[x];
+            const int ca = mt.a_pos / S, sa_ = mt.a_pos % S, cb = mt.b_pos / S, sb_ = mt.b_pos % S;
+            Plan p{-(ca + 1), -(cb + 1), sa_, 0, 0};
+            if (sa_ < sb_)
+                p.src_b = rot_of(1, cb, sb_ - sa_);
+            else if (sb_ < sa_) {
+                p.src_a = rot_of(0, ca, sa_ - sb_);
+                p.min_slot = sb_;
+            }
+            const long long t = (long long)mt.i * job->B.cols + mt.j;
+            p.rc = (int)(t / S);
+            p.rf = (int)(((p.min_slot - t % S) % S + S) % S);
+            plan[x] = p;
         }
-        const long long t = (long long)mt.i * job->B.cols + mt.j;
-        p.rc = (int)(t / S);
-        p.rf = (int)(((p.min_slot - t % S) % S + S) % S);
-        plan[x] = p;
+    } else {
+        // element-wise baselines over row-major dense packing: every kept
+        // product (i, j, k) rotates both operands so its two elements sit in
+        // slot 0 (no reuse between products), then runs Alg. 2's chain
+        const int rows = job->rows, inner = job->inner, cols = job->cols;
+        if (job->Ach.size() != chunks_for((long long)rows * inner, S) ||
+            job->Bch.size() != chunks_for((long long)inner * cols, S))
+            throw Error(SPFHE_EINVAL, "operand chunk count != ceil(elements / S)");
+        if (job->n_c != chunks_for((long long)rows * cols, S))
+            throw Error(SPFHE_EINVAL, "result chunk count != ceil(rows*cols / S)");
+        ell = check_levels_scales(ctx, job->Ach, job->Bch, &job->rscale);
+        auto new_rot = [&](int op, int chunk, int amt) {
+            local_list.push_back(std::make_tuple(op, chunk, amt));
+            partner.push_back(-1);
+            return (int)local_list.size() - 1;
+        };
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j)
+                for (int k = 0; k < inner; ++k) {
+                    const bool a = job->a_nz[(size_t)i * inner + k] != 0, b = job->b_nz[(size_t)k * cols + j] != 0;
+                    if (job->naive == SPFHE_NAIVE_SPARSE && !(a && b)) continue;
+                    if (job->naive == SPFHE_NAIVE_SPARSE_LITERAL && !(a || b)) continue;
+                    const long long pa = (long long)i * inner + k, pb = (long long)k * cols + j;
+                    const int ca = (int)(pa / S), sa_ = (int)(pa % S), cb = (int)(pb / S), sb_ = (int)(pb % S);
+                    Plan p{-(ca + 1), -(cb + 1), 0, 0, 0};
+                    if (sa_) p.src_a = new_rot(0, ca, sa_);
+                    if (sb_) p.src_b = new_rot(1, cb, sb_);
+                    if (p.src_a >= 0 && p.src_b >= 0) {
+                        partner[p.src_a] = p.src_b;
+                        partner[p.src_b] = p.src_a;
+                    }
+                    const long long t = (long long)i * cols + j;
+                    p.rc = (int)(t / S);
+                    p.rf = (int)((S - t % S) % S);
+                    plan.push_back(p);
+                }
     }
+    job->ell = ell;
+    job->id = next_id_++;
+    // keys first: nothing is allocated or launched for a job that would fail
+    if (!plan.empty() && !job->keys->relin) throw Error(SPFHE_EKEY, "no relinearisation key");
     for (auto &r : local_list)
         for (int a : rotation_plan(ctx, std::get<2>(r))) rotation_key(*job->keys, a);
     for (auto &p : plan)
@@ -178,7 +244,7 @@ void Engine::add(Job *job)
             job->C[c] = ct_new(ctx, ell - 2, job->rscale);
             SPFHE_CHECK_CUDA(cudaMemsetAsync(job->C[c]->d, 0, 2ull * (ell - 2) * n * sizeof(u64), ctx.stream));
         }
-        if (!ms.empty()) {
+        if (!plan.empty()) {
             if (job->mask0) {
                 if (job->mask0->level != ell - 1) throw Error(SPFHE_ELEVEL, "mask must be at the operands' level - 1");
                 const size_t words = (size_t)(ell - 1) * n;
@@ -207,16 +273,20 @@ void Engine::add(Job *job)
     // tasks
     LevelQueue &q = levels_[ell];
     const int rot0 = (int)rots_.size();
-    for (auto &r : local_list) rots_.push_back(RotTask{job, std::get<0>(r), std::get<1>(r), std::get<2>(r), {}});
+    for (size_t r = 0; r < local_list.size(); ++r)
+        rots_.push_back(RotTask{job, std::get<0>(local_list[r]), std::get<1>(local_list[r]), std::get<2>(local_list[r]),
+                                {}, partner[r] >= 0 ? rot0 + partner[r] : -1});
     for (auto &p : plan) {
         const int id = (int)matches_.size();
         MatchTask mt{job, p.src_a >= 0 ? rot0 + p.src_a : p.src_a, p.src_b >= 0 ? rot0 + p.src_b : p.src_b,
                      p.min_slot, p.rf, p.rc};
         matches_.push_back(mt);
-        if (mt.src_a >= 0)
-            rots_[mt.src_a].deps.push_back(id);
-        else if (mt.src_b >= 0)
+        // a product whose operands are both rotated waits for the second of
+        // the pair (the two always run in the same wave)
+        if (mt.src_b >= 0)
             rots_[mt.src_b].deps.push_back(id);
+        else if (mt.src_a >= 0)
+            rots_[mt.src_a].deps.push_back(id);
         else
             q.free_matches.push_back(id);
     }
@@ -264,14 +334,20 @@ void Engine::run_wave(int ell, LevelQueue &q)
     const long long csL = 2LL * ell * ctx.n;
     std::vector<int> R;
     while (!q.rots.empty() && (int)R.size() < G) {
-        R.push_back(q.rots.front());
+        const int r = q.rots.front();
+        R.push_back(r);
         q.rots.pop_front();
+        // the partner of a pair (queued right after it) joins the same wave
+        if (rots_[r].partner > r && !q.rots.empty() && q.rots.front() == rots_[r].partner) {
+            R.push_back(q.rots.front());
+            q.rots.pop_front();
+        }
     }
     u64 *align = nullptr;
     std::map<int, int> slot_of;
     std::vector<int> M;
     if (!R.empty()) {
-        align = rt.workspace(WS_ALIGN, (size_t)G * csL);
+        align = rt.workspace(WS_ALIGN, (size_t)(G + 1) * csL);
         std::vector<const Keys *> kk;
         std::vector<const u64 *> in;
         std::vector<int> amt;

@@ -39,6 +39,12 @@ struct Job {
     uint64_t st_matches = 0, st_relin = 0, st_align = 0, st_final = 0, st_rescales = 0, st_launches = 0;
     cudaEvent_t done_ev = nullptr;
     bool finished = false;
+    // element-wise baselines (Sec. 4): -1 = Alg. 1 over CSR x CSC packing;
+    // otherwise SPFHE_NAIVE_* over row-major dense packing, with the zero
+    // patterns (plaintext structure) of A (rows x inner) and B (inner x cols)
+    int naive = -1;
+    int rows = 0, inner = 0, cols = 0;
+    std::vector<uint8_t> a_nz, b_nz;
     // host-side fault injection (tests of the serving loop's error
     // isolation): any wave that would run this job's tasks throws SPFHE_ECUDA
     // before launching anything
@@ -67,6 +73,7 @@ class Engine {
         Job *job;
         int op, chunk, amount;
         std::vector<int> deps;   // match task ids
+        int partner = -1;        // the other operand's rotation of the same product (element-wise baselines)
     };
     struct MatchTask {
         Job *job;
@@ -99,6 +106,10 @@ constexpr int kRelinShare = 8;
 // fill a job from a single-product call (metadata is copied)
 void fill_job(Job &job, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
               const spfhe_sparse_meta &B, Ct *const *Bch, size_t nB, const Pt *mask0, size_t nC);
+// element-wise baselines (Sec. 4) through the engine (spmspm.cpp)
+void naive_ct_ct(Ctx &ctx, const Keys &keys, int mode, int rows, int inner, int cols, const uint8_t *a_nz,
+                 const uint8_t *b_nz, Ct *const *Ach, size_t nA, Ct *const *Bch, size_t nB, const Pt *mask0, Ct **C,
+                 size_t nC, spfhe_stats *out_stats);
 // free a job's private mask copy (and its results when free_results)
 void release_job(Ctx &ctx, Job &job, bool free_results);
 // after release_job(.., true): clear what Engine::add and the waves filled

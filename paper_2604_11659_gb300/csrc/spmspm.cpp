@@ -195,6 +195,51 @@ void spmspm_ct_ct(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *co
     }
 }
 
+void naive_ct_ct(Ctx &ctx, const Keys &keys, int mode, int rows, int inner, int cols, const uint8_t *a_nz,
+                 const uint8_t *b_nz, Ct *const *Ach, size_t nA, Ct *const *Bch, size_t nB, const Pt *mask0, Ct **C,
+                 size_t nC, spfhe_stats *out_stats)
+{
+    const uint64_t launches0 = ctx.launches;
+    if (mode < SPFHE_NAIVE_DENSE || mode > SPFHE_NAIVE_SPARSE_LITERAL) throw Error(SPFHE_EINVAL, "unknown mode");
+    if (rows < 1 || inner < 1 || cols < 1) throw Error(SPFHE_EINVAL, "empty dimension");
+    if ((long long)rows * inner > (1LL << 30) || (long long)inner * cols > (1LL << 30) ||
+        (long long)rows * cols > (1LL << 30))
+        throw Error(SPFHE_EINVAL, "dimensions too large");
+    if (!a_nz || !b_nz) throw Error(SPFHE_EINVAL, "null zero pattern");
+    for (size_t c = 0; c < nC; ++c) C[c] = nullptr;
+    Job job;
+    job.keys = &keys;
+    job.naive = mode;
+    job.rows = rows;
+    job.inner = inner;
+    job.cols = cols;
+    job.a_nz.assign(a_nz, a_nz + (size_t)rows * inner);
+    job.b_nz.assign(b_nz, b_nz + (size_t)inner * cols);
+    job.Ach.assign(Ach, Ach + nA);
+    job.Bch.assign(Bch, Bch + nB);
+    job.mask0 = mask0;
+    job.n_c = nC;
+    Engine eng(ctx);
+    try {
+        eng.add(&job);
+        eng.run_all();
+        ctx_sync(ctx);
+    } catch (...) {
+        release_job(ctx, job, true);
+        throw;
+    }
+    for (size_t c = 0; c < nC; ++c) C[c] = job.C[c];
+    release_job(ctx, job, false);
+    if (out_stats) {
+        out_stats->matches = job.st_matches;
+        out_stats->ks_relin = job.st_relin;
+        out_stats->ks_align = job.st_align;
+        out_stats->ks_final = job.st_final;
+        out_stats->rescales = job.st_rescales;
+        out_stats->launches = ctx.launches - launches0;
+    }
+}
+
 void spmspm_ct_pt(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A, Ct *const *Ach, size_t nA,
                   const spfhe_sparse_meta &B, const double *Bvals, Pt *const *Bpts, Ct **C, size_t nC,
                   spfhe_stats *out_stats)

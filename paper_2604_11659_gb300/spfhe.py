@@ -121,6 +121,10 @@ _SIGS = [
     ("spfhe_sparse_matmul_ct_pt_grouped", ctypes.c_int,
      [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
       c_dblp, ctypes.POINTER(handle), ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
+    ("spfhe_naive_matmul_ct_ct", ctypes.c_int,
+     [handle, handle, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(handle), ctypes.c_size_t, handle,
+      ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(Stats)]),
     ("spfhe_sparse_matmul_ct_ct_grouped", ctypes.c_int,
      [handle, handle, ctypes.POINTER(SparseMeta), ctypes.POINTER(handle), ctypes.c_size_t, ctypes.POINTER(SparseMeta),
       ctypes.POINTER(handle), ctypes.c_size_t, handle, ctypes.c_int, ctypes.POINTER(handle), ctypes.c_size_t,
@@ -594,6 +598,26 @@ def spfhe_server_info(srv):
     ws, used, retried = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().spfhe_server_info(srv, ctypes.byref(ws), ctypes.byref(used), ctypes.byref(retried)))
     return int(ws.value), int(used.value), int(retried.value)
+
+
+NAIVE_DENSE, NAIVE_SPARSE, NAIVE_SPARSE_LITERAL = 0, 1, 2
+
+
+def spfhe_naive_matmul_ct_ct(ctx, keys, mode: int, A_nonzero: np.ndarray, B_nonzero: np.ndarray, A_chunks, B_chunks,
+                             mask0, n_c: int):
+    """Element-wise baseline (Naive Dense / Naive Sparse) over row-major dense
+    packing; A_nonzero / B_nonzero: boolean zero patterns (rows x inner,
+    inner x cols).  Returns (result handles, stats)."""
+    an = np.ascontiguousarray(A_nonzero, dtype=np.uint8)
+    bn = np.ascontiguousarray(B_nonzero, dtype=np.uint8)
+    rows, inner = an.shape
+    cols = bn.shape[1]
+    outs = (handle * n_c)()
+    st = Stats()
+    _check(lib().spfhe_naive_matmul_ct_ct(ctx, keys, int(mode), rows, inner, cols, an.ctypes.data, bn.ctypes.data,
+                                          _handles(A_chunks), len(A_chunks), _handles(B_chunks), len(B_chunks), mask0,
+                                          outs, n_c, ctypes.byref(st)))
+    return [handle(outs[i]) for i in range(n_c)], st.as_dict()
 
 
 def spfhe_sparse_matmul_ct_pt(ctx, keys, A: SparseMeta, A_chunks, B: SparseMeta, B_values, B_pts, n_c: int):

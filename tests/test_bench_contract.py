@@ -121,6 +121,8 @@ def stubbed(monkeypatch):
     monkeypatch.setattr(bench, "batch_vs_plain", lambda *a, **k: {"speedup": 1.7})
     monkeypatch.setattr(bench, "serve_run", lambda *a, **k: {"served": {"p99_ms": 1.0}})
     monkeypatch.setattr(bench, "dense_layer_pt", lambda *a, **k: {"ms": 1.0})
+    monkeypatch.setattr(bench, "naive_sweep", lambda *a, **k: {"rows": []})
+    monkeypatch.setattr(bench, "workload_16x16_end_to_end", lambda *a, **k: {"gpu_ms": 1.0})
     monkeypatch.setattr(bench, "cpu_baseline_line", lambda *a, **k: {"value": 2e-5, "unit": "matmuls/s",
                                                                       "cores": 8, "kind": "oracle", "sample": "s"})
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
@@ -162,17 +164,18 @@ def test_default_line_carries_the_contract(stubbed, monkeypatch, capsys):
                                      "tuner_key_gib": pytest.approx(37251710976 / 2 ** 30)}
     assert line["graph"]["vs_eager"] == pytest.approx(1.0)
     assert line["variant_grouped"]["ks_per_step"] == 11403 + 3003 + 11423
-    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt"):
+    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "naive_sweep_16x16", "workload_16x16"):
         assert k in line
 
 
 def test_skips_leave_their_keys_out(stubbed, monkeypatch, capsys):
     line = _run(monkeypatch, capsys, ["--steps", "1", "--warmup", "3", "--graph-steps", "0", "--grouped-steps", "0",
                                       "--batch-products", "0", "--batch128-products", "0", "--serve-requests", "0",
-                                      "--dense-layer", "0",
+                                      "--dense-layer", "0", "--naive-sweep", "0",
                                       "--no-cpu-baseline"])
     assert line["graph"] is None and line["variant_grouped"] is None
-    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "cpu_baseline"):
+    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "cpu_baseline", "naive_sweep_16x16",
+              "workload_16x16"):
         assert k not in line
     assert line["ms_per_step"] == pytest.approx(STEP_MS)
 
@@ -216,6 +219,7 @@ def _install_stubs(rank):
     bench.batch_vs_plain = lambda *a, **k: {"speedup": 1.7}
     bench.serve_run = lambda *a, **k: {"served": {"p99_ms": 1.0}}
     bench.dense_layer_pt = lambda *a, **k: {"ms": 1.0}
+    bench.naive_sweep = lambda *a, **k: {"rows": []}
 
 
 def _bench_rank(rank, world, port, out_dir):

@@ -31,15 +31,16 @@ METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); key
 ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", "moddown_bconv"}
 
 # DRAM bytes (read + write) per limb of each forward-transform pass kind, from
-# ncu captures of the radix-16 kernels (4 CTAs per SM, split 8/8) on the
-# profiler case (bench.py --small-case: n = 2^16): pass A, pass B, and pass B
-# with the fused ModDown epilogue.
-NTT_FWD_DRAM_PER_LIMB = {"a": (151.2e6 + 90.8e6) / 288, "b": (250.2e6 + 138.6e6) / 345,
-                         "b_moddown": (456.6e6 + 150.7e6) / 288}
+# ncu captures of the radix-16 kernels (kernel variant 5, 4 CTAs per SM, split
+# 8/8) on the profiler case (bench.py --small-case --ntt-chunk 0
+# --ntt-variant 5: n = 2^16): pass A (288 limbs), pass B (345 limbs), and pass
+# B with the fused ModDown epilogue (288 limbs).
+NTT_FWD_DRAM_PER_LIMB = {"a": (151.205e6 + 95.509e6) / 288, "b": (249.898e6 + 142.863e6) / 345,
+                         "b_moddown": (452.206e6 + 140.023e6) / 288}
 
 
 # kernel variant those captures were taken on: traffic is reported only for it
-NTT_FWD_DRAM_VARIANT = 3
+NTT_FWD_DRAM_VARIANT = 5
 
 
 def traffic_source(dom, variant):

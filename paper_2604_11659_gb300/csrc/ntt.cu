@@ -741,7 +741,7 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variants 0, 3, 4 and 5)
+// transforms with a fused prologue / epilogue (kernel variants 0 and 3 to 5)
 template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {

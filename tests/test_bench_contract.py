@@ -258,3 +258,20 @@ def test_two_ranks_print_one_line_with_the_slowest_time(tmp_path):
     assert line["value"] == pytest.approx(2 * 2 / (2 * STEP_MS / 1e3))
     assert "cpu_baseline" not in line
     assert line["variant_grouped"]["ms_per_step"] == pytest.approx(2 * STEP_MS / 2)
+
+
+def test_traffic_reported_for_the_captured_variant(stubbed, monkeypatch, capsys):
+    """When the tuner runs the kernel variant the DRAM counters were captured
+    on, roofline.traffic is the per-launch estimate from the library's limb
+    counts by pass kind, with its ratio to the algorithmic bytes."""
+    orig = FakeMatmul.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        self.ntt_chunk = (bench.NTT_FWD_DRAM_VARIANT, 8, 0)
+    monkeypatch.setattr(FakeMatmul, "__init__", init)
+    line = _run(monkeypatch, capsys, ["--steps", "2", "--warmup", "3"])
+    roof = line["roofline"]
+    want = bench.ks_ntt_fwd_traffic((400.0, 250.0, 150.0), 100)
+    assert roof["traffic"] == pytest.approx(want)
+    assert roof["traffic_over_algorithmic"] == pytest.approx(want / (2.0e12 / 100))

@@ -953,7 +953,7 @@ def main():
     ap.add_argument("--batch128-products", type=int, default=3,
                     help="128x128 products (N=2^16, sparsity U[0.90,0.95]) batched vs one call each (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--graph-steps", type=int, default=2,
                     help="timed launches of the headline product captured as one CUDA graph (0: skip)")
     ap.add_argument("--dense-layer", type=int, default=1,

@@ -261,6 +261,69 @@ __device__ __forceinline__ U128 acc30_value(const Acc30 &a)
     return t;
 }
 
+// The same exact sums with three partial products per term instead of four
+// (Karatsuba on the halves): x c = x0 c0 + ((x0 + x1)(c0 + c1) - x0 c0 -
+// x1 c1) 2^30 + x1 c1 2^60.  s00 and s11 sum x0 c0 and x1 c1 (each term below
+// 2^60: exact for up to 16 terms); the middle products (x0 + x1)(c0 + c1) are
+// below 2^62 and are summed into the 128-bit word (mh, m).  The 128-bit value
+// T is the same integer as with Acc30, so the reduced result is the same.
+struct Acc30K {
+    u64 s00, s11, m, mh;
+};
+
+__device__ __forceinline__ void acc30k_zero(Acc30K &a) { a.s00 = a.s11 = a.m = a.mh = 0; }
+
+// a += x * c for x = (x0, x1) and a split constant c
+__device__ __forceinline__ void acc30k_mac(Acc30K &a, uint32_t x0, uint32_t x1, u64 c)
+{
+    const uint32_t c0 = (uint32_t)c, c1 = (uint32_t)(c >> 32);
+    const uint32_t xs = x0 + x1, cs = c0 + c1;
+    asm("{\n\t.reg .u64 t;\n\t"
+        "mad.wide.u32 %0, %4, %6, %0;\n\t"
+        "mad.wide.u32 %1, %5, %7, %1;\n\t"
+        "mul.wide.u32 t, %8, %9;\n\t"
+        "add.cc.u64 %2, %2, t;\n\t"
+        "addc.u64 %3, %3, 0;\n\t}"
+        : "+l"(a.s00), "+l"(a.s11), "+l"(a.m), "+l"(a.mh)
+        : "r"(x0), "r"(x1), "r"(c0), "r"(c1), "r"(xs), "r"(cs));
+}
+
+// a += x * c for a small x < 2^30 (x1 = 0: the middle product is x (c0 + c1))
+__device__ __forceinline__ void acc30k_mac_small(Acc30K &a, uint32_t x, u64 c)
+{
+    const uint32_t c0 = (uint32_t)c, c1 = (uint32_t)(c >> 32), cs = c0 + c1;
+    asm("{\n\t.reg .u64 t;\n\t"
+        "mad.wide.u32 %0, %3, %4, %0;\n\t"
+        "mul.wide.u32 t, %3, %5;\n\t"
+        "add.cc.u64 %1, %1, t;\n\t"
+        "addc.u64 %2, %2, 0;\n\t}"
+        : "+l"(a.s00), "+l"(a.m), "+l"(a.mh)
+        : "r"(x), "r"(c0), "r"(cs));
+}
+
+// The 128-bit value T of an accumulator.
+__device__ __forceinline__ U128 acc30k_value(const Acc30K &a)
+{
+    // mid = (mh, m) - s00 - s11 = sum of x0 c1 + x1 c0 (below 2^65)
+    u64 ml, mhh;
+    asm("sub.cc.u64 %0, %2, %4;\n\t"
+        "subc.u64 %1, %3, 0;\n\t"
+        "sub.cc.u64 %0, %0, %5;\n\t"
+        "subc.u64 %1, %1, 0;"
+        : "=l"(ml), "=l"(mhh)
+        : "l"(a.m), "l"(a.mh), "l"(a.s00), "l"(a.s11));
+    U128 t;
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u64 %1, %4, %5;"
+        : "=l"(t.lo), "=l"(t.hi)
+        : "l"(a.s00), "l"(ml << 30), "l"((ml >> 34) | (mhh << 30)), "l"(a.s11 >> 4));
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, 0;"
+        : "+l"(t.lo), "+l"(t.hi)
+        : "l"(a.s11 << 60));
+    return t;
+}
+
 // Per-modulus constants (device copy of the host table).
 struct ModConst {
     u64 q;

@@ -56,8 +56,8 @@ __device__ __forceinline__ u64 bconv_out(const u64 *row, const uint32_t (&y0)[NS
 {
     constexpr int RL = bconv_row<NS>();
     const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(row);
-    Acc30 a;
-    acc30_zero(a);
+    Acc30K a;
+    acc30k_zero(a);
     u64 q = 0, qi = 0;
 #pragma unroll
     for (int p = 0; p < RL / 2; ++p) {
@@ -66,13 +66,13 @@ __device__ __forceinline__ u64 bconv_out(const u64 *row, const uint32_t (&y0)[NS
         for (int h = 0; h < 2; ++h) {
             const int e = 2 * p + h;
             const u64 c = h ? w.y : w.x;
-            if (e < NS) acc30_mac(a, y0[e < NS ? e : 0], y1[e < NS ? e : 0], c);
-            else if (e == NS) acc30_mac_small(a, v, c);
+            if (e < NS) acc30k_mac(a, y0[e < NS ? e : 0], y1[e < NS ? e : 0], c);
+            else if (e == NS) acc30k_mac_small(a, v, c);
             else if (e == NS + 1) q = c;
             else if (e == NS + 2) qi = c;
         }
     }
-    return redc(acc30_value(a), q, qi);
+    return redc(acc30k_value(a), q, qi);
 }
 
 // ModUp: for digit j (blockIdx.y) with source limbs [lo, hi) of the
@@ -80,7 +80,8 @@ __device__ __forceinline__ u64 bconv_out(const u64 *row, const uint32_t (&y0)[NS
 // value modulo D = prod q_i into every extended limb t outside [lo, hi):
 //   y_i = [x_i (D/q_i)^{-1}]_{q_i},  v = round(sum_i y_i / q_i) (fma chain),
 //   out_t = sum_i y_i (D/q_i) - v D  mod m_t,
-// one carry-free accumulation (Acc30) of NS + 1 products with Montgomery-form
+// one carry-free accumulation (Acc30K: three 32x32 products per term) of NS + 1
+// products with Montgomery-form
 // constants (the last one v * (-D mod m_t)) and one REDC per output.
 // Extended limb t < ell is q_t, t >= ell is p_{t-ell} (modulus L + t - ell).
 template <int NS>

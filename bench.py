@@ -488,6 +488,46 @@ def batch_vs_plain(stream, count, dims, seed=2, ntt=(5, 0, 0), sparsity=(0.70, 0
     return out
 
 
+def dense_layer_ct_ct(stream, rot_base=16):
+    """The pruned dense layer at the paper's sizing with BOTH operands
+    encrypted (N=2^17, L=35, dnum=5, K=6): 64x784 ReLU-like activations times
+    784x128 N(0, 0.05^2) weights pruned to 90 %, through the lazy-accumulation
+    ct x ct product.  Its 33 471 distinct alignment rotations (73 MB each) do
+    not fit in HBM, so each batch of result groups computes the rotations its
+    matches use and frees them (bounded memory; more alignment key switches).
+    One cold call timed with CUDA events; error against A W in FP64."""
+    import torch
+    from paper_2604_11659_gb300 import params as gparams
+    from paper_2604_11659_gb300 import spfhe as sp
+    from paper_2604_11659_gb300 import synthetic
+    case = synthetic.case_dense_layer(seed=3)
+    rec = case.ring
+    gp = gparams.ctx_params(rec, rot_base=rot_base)
+    ctx = sp.spfhe_ctx_create(gp, stream)
+    keys = sp.spfhe_keygen(ctx, 31)
+    S = (1 << rec.log_n) // 2
+    Am, A_cts, Bm, B_cts, n_c = _encrypt_case(sp, ctx, keys, case, rec.L, rec.scale, 40)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    outs, st = sp.spfhe_sparse_matmul_ct_ct_grouped(ctx, keys, Am, A_cts, Bm, B_cts, None, n_c)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    C = decrypt_matrix(sp, ctx, keys, outs, case.A.shape[0], case.B.shape[1], S)
+    D = C - case.A @ case.B
+    for h in outs + A_cts + B_cts:
+        sp.spfhe_ct_free(h)
+    sp.spfhe_keys_free(keys)
+    sp.spfhe_ctx_destroy(ctx)
+    return {"workload": "64x784 ReLU-like (50 %% zeros) x 784x128 N(0, 0.05^2) pruned to 90 %%, N=2^17, L=35, "
+                        "dnum=5, K=%d, rotation base %d, ct x ct" % (gp.K, rot_base),
+            "variant": "lazy accumulation, alignment rotations streamed per batch of result groups",
+            "matches": st["matches"], "ks_relin": st["ks_relin"], "ks_align": st["ks_align"],
+            "ks_final": st["ks_final"], "ms": ms, "products_per_s": 1e3 / ms, "warmup": 0,
+            "max_abs_err": float(np.max(np.abs(D))), "frobenius_err": float(np.sqrt(np.sum(D * D)))}
+
+
 def naive_sweep(stream, sparsities=(0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0), seed=0, reps=2):
     """The comparison of Sec. 4 / Fig. 4a on the 16x16 workload's ring
     (N=2^12, L=4, dnum=1): CSR/C (Alg. 1 + Alg. 2) against Naive Sparse
@@ -958,6 +998,8 @@ def main():
                     help="timed launches of the headline product captured as one CUDA graph (0: skip)")
     ap.add_argument("--dense-layer", type=int, default=1,
                     help="1: run the N=2^17 dense-layer ct x pt product once (lazy accumulation)")
+    ap.add_argument("--dense-layer-ct-ct", type=int, default=0,
+                    help="1: run the N=2^17 dense layer with both operands encrypted once (minutes)")
     ap.add_argument("--naive-sweep", type=int, default=1,
                     help="1: CSR/C vs Naive Sparse vs Naive Dense over sparsity 0-100 %% at 16x16 (Fig. 4a)")
     ap.add_argument("--grouped-steps", type=int, default=2,
@@ -1206,6 +1248,8 @@ def main():
         line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
     if args.dense_layer:
         line["dense_layer_ct_pt"] = dense_layer_pt(stream)
+    if args.dense_layer_ct_ct:
+        line["dense_layer_ct_ct"] = dense_layer_ct_ct(stream)
     if args.naive_sweep:
         line["naive_sweep_16x16"] = naive_sweep(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -153,6 +153,14 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * EINVAL otherwise.  Results do not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
+/* Device memory (bytes) spfhe_sparse_matmul_ct_ct_grouped may hold in
+ * alignment rotations for a whole call (default: no limit but the free
+ * memory).  Above it, or when they do not fit in the free memory, each batch
+ * of result groups computes the rotations its matches use and frees them
+ * afterwards (more key switches, bounded memory).  Results do not depend on
+ * it. */
+spfhe_status spfhe_ctx_set_align_budget(spfhe_ctx *ctx, uint64_t bytes);
+
 /* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
  * the rescale's spread and last step run inside the forward transforms that
  * feed them (kernel variant 0, 3, 4 or 5, n >= 2^12); 0: as separate kernels.  Results

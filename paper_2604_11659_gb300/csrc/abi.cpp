@@ -191,6 +191,14 @@ spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable)
     });
 }
 
+spfhe_status spfhe_ctx_set_align_budget(spfhe_ctx *ctx, uint64_t bytes)
+{
+    return guard([&] {
+        need(ctx != nullptr, "null context");
+        ctx->c.align_budget = (size_t)bytes;
+    });
+}
+
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {

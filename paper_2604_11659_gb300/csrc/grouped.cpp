@@ -32,9 +32,12 @@
 // tree is complete as soon as the stream has passed its range of amounts and
 // no sum at a lower level within that range is still pending; sums are
 // rotated in batches as they complete, which bounds the tree's memory for
-// any base.  The ct x ct
-// variant keeps every distinct alignment rotation of the call in device memory
-// (checked against the free memory before any launch: ENOMEM otherwise).
+// any base.  The ct x ct variant keeps every distinct alignment rotation of
+// the call in device memory when they fit in the free memory; otherwise it
+// streams them: each batch of groups computes the alignment rotations its
+// matches use (digit by digit as above, restricted to those amounts) and
+// frees them before the next batch, so memory stays bounded at the cost of
+// recomputing rotations that several batches use.  Both give the same bits.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -364,7 +367,18 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             n_rot += st.size();
         }
     for (auto &kv : groups) DigitTree::check_keys(ctx, keys, kv.first.second, merge);
-    need_memory(n_rot * (size_t)csL * sizeof(u64), "the alignment rotations");
+    // every distinct alignment rotation kept for the whole call when it fits;
+    // otherwise (streaming) each batch of groups computes the rotations its
+    // matches use and frees them before the next batch
+    const size_t align_bytes = n_rot * (size_t)csL * sizeof(u64);
+    bool streaming = align_bytes > ctx.align_budget;
+    if (!streaming) {
+        try {
+            need_memory(align_bytes, "the alignment rotations");
+        } catch (const Error &) {
+            streaming = true;
+        }
+    }
 
     uint64_t st_align = 0, st_relin = 0, st_rescales = 0, st_final = 0;
     std::vector<Ct *> res(nC, nullptr);
@@ -393,30 +407,33 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             // needed digit with one hoisted ModUp ----
             const int Bm = match_batch_size(ctx);
             std::vector<const u64 *> aligned(aligns.size(), nullptr);
-            for (auto &kv : by_src) {
-                const u64 *src = (kv.first.first == 0 ? Ach[kv.first.second] : Bch[kv.first.second])->d;
-                std::map<long long, const u64 *> cur{{0, src}};
-                for (long long w = top; w >= 1; w /= b) {
-                    std::map<long long, const u64 *> nxt;
-                    for (auto &ck : cur) {
-                        std::set<int> digs;
-                        for (int a : kv.second) {
-                            const long long amt = std::get<2>(aligns[a]);
-                            if (amt - amt % (w * b) == ck.first) digs.insert((int)((amt / w) % b));
+            auto compute_aligns = [&](const std::map<std::pair<int, int>, std::vector<int>> &srcs, Scratch &mem) {
+                for (auto &kv : srcs) {
+                    const u64 *src = (kv.first.first == 0 ? Ach[kv.first.second] : Bch[kv.first.second])->d;
+                    std::map<long long, const u64 *> cur{{0, src}};
+                    for (long long w = top; w >= 1; w /= b) {
+                        std::map<long long, const u64 *> nxt;
+                        for (auto &ck : cur) {
+                            std::set<int> digs;
+                            for (int a : kv.second) {
+                                const long long amt = std::get<2>(aligns[a]);
+                                if (amt - amt % (w * b) == ck.first) digs.insert((int)((amt / w) % b));
+                            }
+                            std::vector<int> amts;
+                            for (int d : digs)
+                                if (d) amts.push_back((int)(d * w));
+                            u64 *o = amts.empty() ? nullptr : mem.words(amts.size() * (size_t)csL);
+                            rotate_hoisted(ctx, keys, ell, ck.second, amts, o);
+                            st_align += amts.size();
+                            size_t r = 0;
+                            for (int d : digs) nxt[ck.first + d * w] = d ? o + (long long)(r++) * csL : ck.second;
                         }
-                        std::vector<int> amts;
-                        for (int d : digs)
-                            if (d) amts.push_back((int)(d * w));
-                        u64 *o = amts.empty() ? nullptr : sc.words(amts.size() * (size_t)csL);
-                        rotate_hoisted(ctx, keys, ell, ck.second, amts, o);
-                        st_align += amts.size();
-                        size_t r = 0;
-                        for (int d : digs) nxt[ck.first + d * w] = d ? o + (long long)(r++) * csL : ck.second;
+                        cur.swap(nxt);
                     }
-                    cur.swap(nxt);
+                    for (int a : kv.second) aligned[a] = cur.at(std::get<2>(aligns[a]));
                 }
-                for (int a : kv.second) aligned[a] = cur.at(std::get<2>(aligns[a]));
-            }
+            };
+            if (!streaming) compute_aligns(by_src, sc);
             auto operand = [&](int src, bool a_side) -> const u64 * {
                 if (src < 0) return (a_side ? Ach[-src - 1] : Bch[-src - 1])->d;
                 return aligned[src];
@@ -426,9 +443,63 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
             std::vector<const std::pair<const Key, std::vector<int>> *> gl;
             for (auto &kv : groups) gl.push_back(&kv);
             const size_t max_matches = (size_t)2 * Bm;
-            for (size_t gi = 0; gi < gl.size(); gi += Bm) {
-                const size_t ge = std::min(gl.size(), gi + Bm);
+            // batches of at most Bm groups; streaming: also at most as many
+            // as keep the batch's alignment rotations (every ciphertext the
+            // digit-by-digit process creates for them) within half the free
+            // memory left after a margin
+            std::vector<size_t> ends;
+            if (!streaming) {
+                for (size_t gi = 0; gi < gl.size(); gi += Bm) ends.push_back(std::min(gl.size(), gi + Bm));
+            } else {
+                size_t free_b = 0, total_b = 0;
+                SPFHE_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+                const size_t margin = (size_t)8 << 30;
+                const size_t limit_cts =
+                    std::max<size_t>(1, (free_b > margin ? (free_b - margin) / 2 : 0) / ((size_t)csL * sizeof(u64)));
+                std::set<std::tuple<int, int, long long, long long>> nodes;   // (operand, chunk, stage, prefix + digit)
+                std::set<int> seen;
+                size_t gi = 0;
+                for (size_t g = 0; g < gl.size(); ++g) {
+                    std::vector<std::tuple<int, int, long long, long long>> add;
+                    for (int x : gl[g]->second)
+                        for (int a : {pm[x].src_a, pm[x].src_b}) {
+                            if (a < 0 || seen.count(a)) continue;
+                            const long long amt = std::get<2>(aligns[a]);
+                            for (long long w = top; w >= 1; w /= b)
+                                if ((amt / w) % b)
+                                    add.emplace_back(std::get<0>(aligns[a]), std::get<1>(aligns[a]), w,
+                                                     amt - amt % w);
+                        }
+                    size_t extra = 0;
+                    for (auto &t : add) extra += nodes.count(t) ? 0 : 1;
+                    if (g > gi && (g - gi >= (size_t)Bm || nodes.size() + extra > limit_cts)) {
+                        ends.push_back(g);
+                        gi = g;
+                        nodes.clear();
+                        seen.clear();
+                    }
+                    for (auto &t : add) nodes.insert(t);
+                    for (int x : gl[g]->second)
+                        for (int a : {pm[x].src_a, pm[x].src_b})
+                            if (a >= 0) seen.insert(a);
+                }
+                ends.push_back(gl.size());
+            }
+            for (size_t bi = 0, gi = 0; bi < ends.size(); gi = ends[bi++]) {
+                const size_t ge = ends[bi];
                 const int k = (int)(ge - gi);
+                // streaming: this batch's alignment rotations, freed at its end
+                Scratch batch_mem(ctx);
+                if (streaming) {
+                    std::map<std::pair<int, int>, std::vector<int>> need;
+                    std::set<int> seen;
+                    for (size_t g = gi; g < ge; ++g)
+                        for (int x : gl[g]->second)
+                            for (int a : {pm[x].src_a, pm[x].src_b})
+                                if (a >= 0 && seen.insert(a).second)
+                                    need[{std::get<0>(aligns[a]), std::get<1>(aligns[a])}].push_back(a);
+                    compute_aligns(need, batch_mem);
+                }
                 u64 *G = rt.workspace(WS_GRP_SUM, (size_t)k * t3L);
                 u64 *R1 = rt.workspace(WS_LEVEL1, (size_t)k * t31);
                 u64 *R2 = rt.workspace(WS_LEVEL2, (size_t)k * cs1);

@@ -112,6 +112,9 @@ struct Ctx {
     int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
     int ntt_variant = 5;             // radix-16 kernel variant (0 to 5)
     bool fuse_epilogues = true;      // ModDown / rescale epilogues inside the forward transform
+    // device memory the grouped ct x ct product may hold in alignment
+    // rotations for the whole call; above it they are streamed per batch
+    size_t align_budget = SIZE_MAX;
     // while a CUDA graph is being captured: its own buffers (graph.cpp)
     struct Capture *cap = nullptr;
 };

@@ -64,6 +64,7 @@ _SIGS = [
     ("spfhe_ctx_set_match_batch", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_ctx_set_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_ctx_set_ntt_split", ctypes.c_int, [handle, ctypes.c_uint32]),
+    ("spfhe_ctx_set_align_budget", ctypes.c_int, [handle, ctypes.c_uint64]),
     ("spfhe_ctx_set_ntt_variant", ctypes.c_int, [handle, ctypes.c_uint32]),
     ("spfhe_ctx_set_fusion", ctypes.c_int, [handle, ctypes.c_int]),
     ("spfhe_tune_ntt_chunk", ctypes.c_int, [handle, ctypes.c_uint32, ctypes.c_uint32,
@@ -253,6 +254,10 @@ def spfhe_ctx_set_ntt_split(ctx, pass_a_stages: int):
 
 def spfhe_ctx_set_fusion(ctx, enable: bool):
     _check(lib().spfhe_ctx_set_fusion(ctx, 1 if enable else 0))
+
+
+def spfhe_ctx_set_align_budget(ctx, nbytes: int):
+    _check(lib().spfhe_ctx_set_align_budget(ctx, int(nbytes)))
 
 
 def spfhe_ctx_set_ntt_variant(ctx, variant: int):

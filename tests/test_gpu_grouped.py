@@ -72,6 +72,27 @@ def test_grouped_small_match_batches_and_big_groups():
         p.close()
 
 
+@pytest.mark.parametrize("batch", [2, 32])
+def test_grouped_streamed_alignments_bit_exact(batch):
+    """With an alignment-memory budget of zero every batch of groups computes
+    the alignment rotations its matches use and frees them afterwards: the
+    results are the oracle's bits, relinearisation and final-rotation counts
+    unchanged, alignment key switches at least the kept-for-the-call count."""
+    case = CASES["multi_chunk_8x8_b4"]()
+    p = _setup(case, rot_base=4)
+    try:
+        p.spfhe.spfhe_ctx_set_align_budget(p.ctx, 0)
+        p.spfhe.spfhe_ctx_set_match_batch(p.ctx, batch)
+        want, outs, stats, counts = _run_grouped(p, True)
+        for h, w in zip(outs, want):
+            p.assert_ct_equal(h, w)
+        for k in ("matches", "ks_relin", "ks_final", "rescales"):
+            assert stats[k] == getattr(counts, k), k
+        assert stats["ks_align"] >= counts.ks_align
+    finally:
+        p.close()
+
+
 def test_grouped_library_mask_decrypts():
     """With the library's own mask (its encoder agrees with the oracle's to
     +-1 per coefficient, so no bit parity): within 1e-4 of FP64."""

@@ -1246,6 +1246,12 @@ def main():
                                                sparsity=(0.90, 0.95), op_by_op=False, warmup=False)
     if args.serve_requests > 0:
         line["serve"] = serve_run(stream, args.serve_requests, (8, 16), args.serve_rate, ntt=g.ntt_chunk)
+        proj = line["serve"].get("stated_stream_projection")
+        if proj:
+            # the stated stream's requests fill every launch as the headline's product does
+            rate = st["matches"] / (ms_step / 1e3)
+            proj["headline_matches_per_s"] = rate
+            proj["projected_hours_at_headline_rate"] = proj["matches"] / rate / 3600.0
     if args.dense_layer:
         line["dense_layer_ct_pt"] = dense_layer_pt(stream)
     if args.dense_layer_ct_ct:

@@ -203,7 +203,7 @@ spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {
         need(ctx != nullptr, "null context");
-        need(variant <= 5, "NTT variant must be 0 to 5");
+        need(variant <= 6, "NTT variant must be 0 to 6");
         ctx->c.ntt_variant = (int)variant;
     });
 }

@@ -372,9 +372,11 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 //   4: as 3 with the Shoup products split into single-word halves
 //      (mul_shoup3s; the same bits);
 //   5: as 4 with the quotient's low middle halves dropped (mul_shoup4s,
-//      products in [0, 4q); the transforms' outputs are the same residues).
+//      products in [0, 4q); the transforms' outputs are the same residues);
+//   6: as 5 with pass B synchronising warps instead of the CTA (r16_sync).
 template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V >= 3 ? 4 : 2); }
-template <int V> constexpr int r16_arith() { return V == 5 ? 2 : (V == 4 ? 1 : 0); }
+template <int V> constexpr int r16_arith() { return V >= 5 ? 2 : (V == 4 ? 1 : 0); }
+template <int V> constexpr bool r16_warp_local() { return V == 6; }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -398,6 +400,23 @@ __device__ __forceinline__ void r16_prefetch_wait()
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 }
+
+// Pass B exchanges data only inside a tile, and a tile (2^P elements, 16
+// per thread) never spans two warps: with WL ("warp-local") the transposes
+// synchronise the warp instead of the CTA, and every warp stages and stores
+// its own 512 contiguous elements, so pass B has no CTA-wide barrier.
+template <bool WL> __device__ __forceinline__ void r16_sync()
+{
+    if constexpr (WL) __syncwarp();
+    else __syncthreads();
+}
+// loop over the CTA's elements (all of them, or the calling warp's 512)
+template <bool WL> __device__ __forceinline__ int r16_first()
+{
+    return WL ? (int)(threadIdx.x & ~31u) * 16 + (int)(threadIdx.x & 31u) : (int)threadIdx.x;
+}
+template <bool WL> __device__ __forceinline__ int r16_end() { return WL ? (int)(threadIdx.x & ~31u) * 16 + 512 : kElems; }
+template <bool WL> constexpr int r16_step() { return WL ? 32 : 256; }
 
 template <int P, bool LAZY, int MODE, int AR = 0>
 __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulonglong2 *__restrict__ w2, int log_n,
@@ -465,7 +484,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a,
     else fwd16_a_body<P, false, MODE, AR>(sm, p, q, w2, log_n, f, mc);
 }
 
-template <int P, bool LAZY, bool SM, int MODE = kFuseNone, int AR = 0>
+template <int P, bool LAZY, bool SM, int MODE = kFuseNone, int AR = 0, bool WL = false>
 __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m, const ulonglong2 *__restrict__ w2,
                                              int PA, const ulonglong2 *smt, const FuseArgs &f = FuseArgs{},
                                              int log_n = 0)
@@ -485,28 +504,28 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
     if constexpr (R > 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))] = v[i];
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))];
         r16_fwd_round<P, 1, LAZY, SM, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 2) {
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))] = v[i];
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 2>(t, i))];
         r16_fwd_round<P, 2, LAZY, SM, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     // the last round holds 16 contiguous elements per thread: stage through
     // shared memory so the global stores are coalesced
-    __syncthreads();
+    r16_sync<WL>();
 #pragma unroll
     for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
-    __syncthreads();
+    r16_sync<WL>();
     if constexpr (MODE == kFuseNone) {
-        for (int x = threadIdx.x; x < kElems; x += 256) {
+        for (int x = r16_first<WL>(); x < r16_end<WL>(); x += r16_step<WL>()) {
             const u64 y = sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))];
             p[e0 + x] = reduce_any(y, q, m.one_p);
         }
@@ -523,17 +542,17 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         const unsigned g = f.base_g ? (unsigned)f.base_g[it] : 1u;
         u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
         // eight elements per thread at a time: all their loads in flight together
-        for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+        for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
             u64 av[8], bv[8];
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const size_t k = e0 + x0 + r * 256;
+                const size_t k = e0 + x0 + r * r16_step<WL>();
                 av[r] = acc[k];
                 bv[r] = add_base ? base[f.base_g ? perm_index((int)k, g, log_n) : (int)k] : 0;
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int x = x0 + r * 256;
+                const int x = x0 + r * r16_step<WL>();
                 const u64 c = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
                 u64 v = mul_shoup(sub_mod(av[r], c, q), pinv, pinvp, q);
                 if (add_base) v = add_mod(v, bv[r], q);
@@ -547,13 +566,13 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         const u64 inv = __ldg(f.inv + i), invp = __ldg(f.invp + i);
         const u64 *__restrict__ in = f.in[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
         u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
-        for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+        for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
             u64 cv[8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) cv[r] = in[e0 + x0 + r * 256];
+            for (int r = 0; r < 8; ++r) cv[r] = in[e0 + x0 + r * r16_step<WL>()];
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int x = x0 + r * 256;
+                const int x = x0 + r * r16_step<WL>();
                 const u64 rr = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
                 out[e0 + x] = mul_shoup(sub_mod(cv[r], rr, q), inv, invp, q);
             }
@@ -574,17 +593,18 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a,
     const ModConst m = mc[mi];
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     constexpr int AR = r16_arith<V>();
+    constexpr bool WL = r16_warp_local<V>();
     constexpr u64 LB = lazy_fwd_bound<AR>();
     if constexpr (MODE != kFuseNone) {
-        if (m.q < LB) fwd16_b_body<P, true, false, MODE, AR>(sm, p, m, w2, PA, nullptr, f, log_n);
-        else fwd16_b_body<P, false, false, MODE, AR>(sm, p, m, w2, PA, nullptr, f, log_n);
+        if (m.q < LB) fwd16_b_body<P, true, false, MODE, AR, WL>(sm, p, m, w2, PA, nullptr, f, log_n);
+        else fwd16_b_body<P, false, false, MODE, AR, WL>(sm, p, m, w2, PA, nullptr, f, log_n);
     } else if constexpr (V == 2) {
         r16_prefetch_tw<P>(smt, w2, PA, (int)(((size_t)blockIdx.x * kElems) >> P));
         if (m.q < LB) fwd16_b_body<P, true, true>(sm, p, m, w2, PA, smt);
         else fwd16_b_body<P, false, true>(sm, p, m, w2, PA, smt);
     } else {
-        if (m.q < LB) fwd16_b_body<P, true, false, kFuseNone, AR>(sm, p, m, w2, PA, nullptr);
-        else fwd16_b_body<P, false, false, kFuseNone, AR>(sm, p, m, w2, PA, nullptr);
+        if (m.q < LB) fwd16_b_body<P, true, false, kFuseNone, AR, WL>(sm, p, m, w2, PA, nullptr);
+        else fwd16_b_body<P, false, false, kFuseNone, AR, WL>(sm, p, m, w2, PA, nullptr);
     }
 }
 
@@ -597,6 +617,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
     constexpr bool SM = V == 2;
     constexpr int AR = r16_arith<V>();
+    constexpr bool WL = r16_warp_local<V>();
     constexpr int TPT = 1 << (P - 4);
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
@@ -615,36 +636,36 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     else r16_load_tw<P, R - 1, Q1, Q1 - 1, false>(wpre, t, w2, PA, btile, nullptr, 0);
     // loads before stores, eight at a time (the stores into shared memory
     // would otherwise wait for each load in turn)
-    for (int x0 = threadIdx.x; x0 < kElems; x0 += 8 * 256) {
+    for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
         u64 tmp[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) tmp[r] = p[e0 + x0 + r * 256];
+        for (int r = 0; r < 8; ++r) tmp[r] = p[e0 + x0 + r * r16_step<WL>()];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            const int x = x0 + r * 256;
+            const int x = x0 + r * r16_step<WL>();
             sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))] = tmp[r];
         }
     }
     if constexpr (SM) r16_prefetch_wait();
-    else __syncthreads();
+    else r16_sync<WL>();
     u64 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))];
     r16_inv_round<P, R - 1, SM, !SM, AR>(v, t, w2, q, PA, btile, smt, tile, &wpre);
     if constexpr (R > 2) {
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, R - 1>(t, i))] = v[i];
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, R - 2>(t, i))];
         r16_inv_round<P, R - 2, SM, false, AR>(v, t, w2, q, PA, btile, smt, tile);
     }
     if constexpr (R > 1) {
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[r16_slot_b<P>(tile, r16_index<P, 1>(t, i))] = v[i];
-        __syncthreads();
+        r16_sync<WL>();
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_b<P>(tile, r16_index<P, 0>(t, i))];
         r16_inv_round<P, 0, SM, false, AR>(v, t, w2, q, PA, btile, smt, tile);
@@ -741,7 +762,7 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variants 0 and 3 to 5)
+// transforms with a fused prologue / epilogue (kernel variants 0 and 3 to 6)
 template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
@@ -757,14 +778,16 @@ template <int P, int V> struct R16FusedV {
 template <int P> struct R16Fused {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_a(g, s, a, c, mode, f);
+        if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_a(g, s, a, c, mode, f);
+        else if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
         else R16FusedV<P, 0>::fwd_a(g, s, a, c, mode, f);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_b(g, s, a, c, PA, mode, f);
+        if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_b(g, s, a, c, PA, mode, f);
+        else if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
         else R16FusedV<P, 0>::fwd_b(g, s, a, c, PA, mode, f);
@@ -781,6 +804,7 @@ template <int P> struct R16Launch {
         case 3: f(R16LaunchV<P, 3>{}); break;
         case 4: f(R16LaunchV<P, 4>{}); break;
         case 5: f(R16LaunchV<P, 5>{}); break;
+        case 6: f(R16LaunchV<P, 6>{}); break;
         default: throw Error(SPFHE_EINVAL, "no such NTT variant");
         }
     }

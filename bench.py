@@ -237,7 +237,7 @@ def tune_ntt(sp, ctx, rec, chunk, variant=0):
     items = 32 if rec.log_n >= 15 else 64
     splits = [pa for pa in range(6, 10) if 6 <= rec.log_n - pa <= 9] if rec.log_n >= 12 else [0]
     best, timings = None, {}
-    for var in (0, 1, 2, 3, 4, 5, 6, 7):
+    for var in (0, 1, 2, 3, 4, 5, 6):
         sp.spfhe_ctx_set_ntt_variant(ctx, var)
         for pa in splits:
             sp.spfhe_ctx_set_ntt_split(ctx, pa)

@@ -151,9 +151,8 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * one 64-bit-result multiply; 5 (default) = as 4 with a shorter quotient
  * estimate (products in [0, 4q), intermediate values kept below 8q); 6 = as
  * 5 with the second pass synchronising warps instead of whole CTAs (a tile
- * of the second pass never spans two warps); 7 = as 6 with each CTA asking
- * L2 for the data of the CTA launched 4 x (SM count) positions after it.
- * EINVAL otherwise.  Results do not depend on it. */
+ * of the second pass never spans two warps).  EINVAL otherwise.  Results do
+ * not depend on it. */
 spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant);
 
 /* Device memory (bytes) spfhe_sparse_matmul_ct_ct_grouped may hold in
@@ -166,7 +165,7 @@ spfhe_status spfhe_ctx_set_align_budget(spfhe_ctx *ctx, uint64_t bytes);
 
 /* enable != 0 (default): ModDown's last step ((acc - conv) P^{-1} + base) and
  * the rescale's spread and last step run inside the forward transforms that
- * feed them (kernel variant 0 or 3 to 7, n >= 2^12); 0: as separate kernels.  Results
+ * feed them (kernel variant 0 or 3 to 6, n >= 2^12); 0: as separate kernels.  Results
  * do not depend on it. */
 spfhe_status spfhe_ctx_set_fusion(spfhe_ctx *ctx, int enable);
 

@@ -98,7 +98,6 @@ spfhe_status spfhe_ctx_create(const spfhe_params *params, void *cuda_stream, spf
         try {
             Ctx &c = h->c;
             SPFHE_CHECK_CUDA(cudaGetDevice(&c.device));
-            SPFHE_CHECK_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
             c.stream = static_cast<cudaStream_t>(cuda_stream);
             configure_pool(c.device);
             build_params(c, *params);
@@ -204,7 +203,7 @@ spfhe_status spfhe_ctx_set_ntt_variant(spfhe_ctx *ctx, uint32_t variant)
 {
     return guard([&] {
         need(ctx != nullptr, "null context");
-        need(variant <= 7, "NTT variant must be 0 to 7");
+        need(variant <= 6, "NTT variant must be 0 to 6");
         ctx->c.ntt_variant = (int)variant;
     });
 }

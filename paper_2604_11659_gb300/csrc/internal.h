@@ -98,7 +98,6 @@ struct Ctx {
     std::vector<ModConst> mc;
     cudaStream_t stream = nullptr;
     int device = 0;
-    int num_sms = 0;                 // multiprocessors of the device
     DevTables dt;
     // the library's own one-hot slot-0 masks (Montgomery form) per operand
     // level ell: [ell-1][n] at scale q_{ell-2}, built on first use

@@ -33,10 +33,6 @@ struct NttArgs {
     long long stride;
     const int *ids;
     LimbMap map;
-    // > 0: each CTA of a radix-16 pass first asks L2 for the tile of the CTA
-    // launched `ahead` positions after it (the one likely to start when a
-    // CTA slot frees up), so that CTA's loads find its data in L2
-    int ahead = 0;
 };
 
 __device__ __forceinline__ u64 *limb_ptr(const NttArgs &a, int n, int &mi)
@@ -45,33 +41,6 @@ __device__ __forceinline__ u64 *limb_ptr(const NttArgs &a, int n, int &mi)
     const long long item = a.ids ? a.ids[blockIdx.z] : blockIdx.z;
     mi = a.map.mi[slot];
     return a.base + item * a.stride + (long long)a.map.off[slot] * n;
-}
-
-// L2 prefetch of the 32 KB tile of the CTA launched a.ahead positions after
-// this one (one 128-byte line per thread); PASS_A: its 2^P strided rows of
-// 4096 >> P elements, else 4096 contiguous elements.  Nothing past the grid.
-template <int P, bool PASS_A> __device__ __forceinline__ void r16_prefetch_ahead(const NttArgs &a, int log_n)
-{
-    if (a.ahead <= 0) return;
-    const long long gx = gridDim.x, gy = gridDim.y;
-    const long long lin = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) + a.ahead;
-    if (lin >= gx * gy * (long long)gridDim.z) return;
-    const int x = (int)(lin % gx), y = (int)((lin / gx) % gy), z = (int)(lin / (gx * gy));
-    const long long item = a.ids ? a.ids[z] : z;
-    const u64 *limb = a.base + item * a.stride + ((long long)a.map.off[y] << log_n);
-    const u64 *line;
-    if constexpr (PASS_A) {
-        constexpr int TPC = 4096 >> P;                      // columns of the tile (8..64)
-        constexpr int LPR = TPC >= 16 ? TPC / 16 : 1;       // 128-byte lines per row
-        for (int k = threadIdx.x; k < (1 << P) * LPR; k += 256) {
-            const int row = k / LPR, part = k % LPR;
-            line = limb + ((size_t)row << (log_n - P)) + (size_t)x * TPC + part * 16;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
-        }
-    } else {
-        line = limb + (size_t)x * 4096 + threadIdx.x * 16;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
-    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_fwd_a(NttArgs a, const ModConst *__restrict__ mc,
@@ -404,12 +373,10 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 //      (mul_shoup3s; the same bits);
 //   5: as 4 with the quotient's low middle halves dropped (mul_shoup4s,
 //      products in [0, 4q); the transforms' outputs are the same residues);
-//   6: as 5 with pass B synchronising warps instead of the CTA (r16_sync);
-//   7: as 6 with each CTA asking L2 for the tile of the CTA launched 4 x
-//      (SMs) positions after it (r16_prefetch_ahead).
+//   6: as 5 with pass B synchronising warps instead of the CTA (r16_sync).
 template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V >= 3 ? 4 : 2); }
 template <int V> constexpr int r16_arith() { return V >= 5 ? 2 : (V == 4 ? 1 : 0); }
-template <int V> constexpr bool r16_warp_local() { return V >= 6; }
+template <int V> constexpr bool r16_warp_local() { return V == 6; }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -508,7 +475,6 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_a(NttArgs a,
 {
     __shared__ u64 sm[r16_smem_words_a<P>()];
     const int n = 1 << log_n;
-    r16_prefetch_ahead<P, true>(a, log_n);
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
@@ -622,7 +588,6 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_fwd16_b(NttArgs a,
     __shared__ u64 sm[r16_smem_words_b<P>()];
     extern __shared__ __align__(16) ulonglong2 smt[];   // V == 2: [r16_tw_smem_entries<P>()]
     const int n = 1 << log_n;
-    r16_prefetch_ahead<P, false>(a, log_n);
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
@@ -656,7 +621,6 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     constexpr int TPT = 1 << (P - 4);
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
-    r16_prefetch_ahead<P, false>(a, log_n);
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const u64 q = mc[mi].q;
@@ -719,7 +683,6 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
     constexpr int TPC = kElems >> P;
     constexpr int R = (P + 3) / 4;
     const int n = 1 << log_n;
-    r16_prefetch_ahead<P, true>(a, log_n);
     int mi;
     u64 *p = limb_ptr(a, n, mi);
     const ModConst m = mc[mi];
@@ -799,7 +762,7 @@ template <int P, int V> struct R16LaunchV {
     }
 };
 
-// transforms with a fused prologue / epilogue (kernel variants 0 and 3 to 7)
+// transforms with a fused prologue / epilogue (kernel variants 0 and 3 to 6)
 template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
@@ -815,8 +778,7 @@ template <int P, int V> struct R16FusedV {
 template <int P> struct R16Fused {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 7) R16FusedV<P, 7>::fwd_a(g, s, a, c, mode, f);
-        else if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_a(g, s, a, c, mode, f);
+        if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_a(g, s, a, c, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_a(g, s, a, c, mode, f);
@@ -824,8 +786,7 @@ template <int P> struct R16Fused {
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
-        if (c.ntt_variant == 7) R16FusedV<P, 7>::fwd_b(g, s, a, c, PA, mode, f);
-        else if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_b(g, s, a, c, PA, mode, f);
+        if (c.ntt_variant == 6) R16FusedV<P, 6>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 5) R16FusedV<P, 5>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 4) R16FusedV<P, 4>::fwd_b(g, s, a, c, PA, mode, f);
         else if (c.ntt_variant == 3) R16FusedV<P, 3>::fwd_b(g, s, a, c, PA, mode, f);
@@ -844,7 +805,6 @@ template <int P> struct R16Launch {
         case 4: f(R16LaunchV<P, 4>{}); break;
         case 5: f(R16LaunchV<P, 5>{}); break;
         case 6: f(R16LaunchV<P, 6>{}); break;
-        case 7: f(R16LaunchV<P, 7>{}); break;
         default: throw Error(SPFHE_EINVAL, "no such NTT variant");
         }
     }
@@ -963,9 +923,6 @@ LimbMap limb_range(int first_off, int count, int first_mi)
     return m;
 }
 
-// variant 7's prefetch distance: the CTAs resident at once (4 per SM)
-static int r16_ahead(const Ctx &ctx) { return ctx.ntt_variant == 7 && ctx.log_n >= 12 ? 4 * ctx.num_sms : 0; }
-
 // stages in pass A of the radix-16 transforms (the rest run in pass B)
 static int pass_a_stages(const Ctx &ctx) { return ctx.ntt_pa ? ctx.ntt_pa : ctx.log_n / 2; }
 
@@ -974,12 +931,12 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map)
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return;
     Geometry g = geometry(ctx.log_n);
-    NttArgs a{b.base, b.stride, b.ids, map, r16_ahead(ctx)};
+    NttArgs a{b.base, b.stride, b.ids, map};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD;
     if (ctx.log_n >= 12) {
         const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
         for_chunks(ctx, b, map, [&](const Batch &cb, const LimbMap &cm) {
-            NttArgs ca{cb.base, cb.stride, cb.ids, cm, r16_ahead(ctx)};
+            NttArgs ca{cb.base, cb.stride, cb.ids, cm};
             dim3 grid(ctx.n / kElems, cm.nl, cb.items);
             {
                 cudaEvent_t t0_ = prof_begin(ctx);
@@ -1017,7 +974,7 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
         return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
-    NttArgs a{b.base, b.stride, b.ids, map, r16_ahead(ctx)};
+    NttArgs a{b.base, b.stride, b.ids, map};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_FWD : K_NTT_FWD;
     const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
     dim3 grid(ctx.n / kElems, map.nl, b.items);
@@ -1050,12 +1007,12 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return;
     Geometry g = geometry(ctx.log_n);
-    NttArgs a{b.base, b.stride, b.ids, map, r16_ahead(ctx)};
+    NttArgs a{b.base, b.stride, b.ids, map};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV;
     if (ctx.log_n >= 12) {
         const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
         for_chunks(ctx, b, map, [&](const Batch &cb, const LimbMap &cm) {
-            NttArgs ca{cb.base, cb.stride, cb.ids, cm, r16_ahead(ctx)};
+            NttArgs ca{cb.base, cb.stride, cb.ids, cm};
             dim3 grid(ctx.n / kElems, cm.nl, cb.items);
             {
                 cudaEvent_t t0_ = prof_begin(ctx);

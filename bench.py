@@ -370,7 +370,7 @@ def product_errors(errs):
     return {"max_abs_err": max(e[0] for e in errs), "frobenius_err": max(e[1] for e in errs), "checked": len(errs)}
 
 
-def batch_vs_plain(stream, count, dims, seed=2, ntt=(5, 0, 0), sparsity=(0.70, 0.95), op_by_op=True, warmup=True):
+def batch_vs_plain(stream, count, dims, seed=2, ntt=(6, 0, 0), sparsity=(0.70, 0.95), op_by_op=True, warmup=True):
     """`count` products of the batch workload's recipe (d from `dims`,
     sparsity uniform in `sparsity`, half Bernoulli / half 2:4) on its ring
     (N=2^16, L=20, dnum=4): one spfhe_sparse_matmul_batch call, and the same
@@ -732,7 +732,7 @@ def dense_layer_pt(stream, rot_base=16):
             "ms": ms, "products_per_s": 1e3 / ms, "warmup": 0, "max_abs_err": err, "keygen_s": round(keygen_s, 2)}
 
 
-def serve_run(stream, count, dims, rate, seed=4, ntt=(5, 0, 0), project=2000):
+def serve_run(stream, count, dims, rate, seed=4, ntt=(6, 0, 0), project=2000):
     """Poisson stream of `count` requests (d from `dims`, sparsity U[0.5,0.95],
     remaining levels U{10..30}, 4 key sets) on the serving ring (N=2^16, L=31,
     dnum=4): the continuous-batching server against the plain path, which
@@ -1007,7 +1007,7 @@ def main():
     ap.add_argument("--ntt-chunk", type=int, default=-1,
                     help="limbs per NTT launch pair; -1 = autotune on the workload's key-switch shape")
     ap.add_argument("--small-batch", type=int, default=8)
-    ap.add_argument("--ntt-variant", type=int, default=0, help="NTT kernel variant when --ntt-chunk is given")
+    ap.add_argument("--ntt-variant", type=int, default=6, help="NTT kernel variant when --ntt-chunk is given")
     ap.add_argument("--small-case", action="store_true",
                     help="profiler case: three relinearised products (tensor + key switch) at the workload's ring")
     args = ap.parse_args()

@@ -148,8 +148,8 @@ spfhe_status spfhe_ctx_set_ntt_split(spfhe_ctx *ctx, uint32_t pass_a_stages);
  * (about 64 KB of dynamic shared memory per CTA); 3 = as 0 with the register
  * budget of 4 CTAs per SM; 4 = as 3 with every 32x32-bit partial product of
  * the Shoup multiplications taken as separate low and high halves instead of
- * one 64-bit-result multiply; 5 (default) = as 4 with a shorter quotient
- * estimate (products in [0, 4q), intermediate values kept below 8q); 6 = as
+ * one 64-bit-result multiply; 5 = as 4 with a shorter quotient estimate
+ * (products in [0, 4q), intermediate values kept below 8q); 6 (default) = as
  * 5 with the second pass synchronising warps instead of whole CTAs (a tile
  * of the second pass never spans two warps).  EINVAL otherwise.  Results do
  * not depend on it. */

@@ -110,7 +110,7 @@ struct Ctx {
     int match_batch = 0;             // matches per batch (0: default for the ring size)
     int ntt_chunk = 0;               // limbs per pass-A/pass-B launch pair (0: whole batch)
     int ntt_pa = 0;                  // stages in NTT pass A for n >= 2^12 (0: log_n / 2)
-    int ntt_variant = 5;             // radix-16 kernel variant (0 to 5)
+    int ntt_variant = 6;             // radix-16 kernel variant (0 to 6)
     bool fuse_epilogues = true;      // ModDown / rescale epilogues inside the forward transform
     // device memory the grouped ct x ct product may hold in alignment
     // rotations for the whole call; above it they are streamed per batch

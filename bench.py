@@ -31,16 +31,16 @@ METRIC = "encrypted 128x128 sparse matmuls/sec at N=2^16 (batched vs plain); key
 ALU_CLASSES = {"ntt_fwd", "ntt_inv", "ks_ntt_fwd", "ks_ntt_inv", "modup_bconv", "moddown_bconv"}
 
 # DRAM bytes (read + write) per limb of each forward-transform pass kind, from
-# ncu captures of the radix-16 kernels (kernel variant 5, 4 CTAs per SM, split
+# ncu captures of the radix-16 kernels (kernel variant 6, 4 CTAs per SM, split
 # 8/8) on the profiler case (bench.py --small-case --ntt-chunk 0
-# --ntt-variant 5: n = 2^16): pass A (288 limbs), pass B (345 limbs), and pass
+# --ntt-variant 6: n = 2^16): pass A (288 limbs), pass B (345 limbs), and pass
 # B with the fused ModDown epilogue (288 limbs).
-NTT_FWD_DRAM_PER_LIMB = {"a": (151.205e6 + 95.509e6) / 288, "b": (249.898e6 + 142.863e6) / 345,
-                         "b_moddown": (452.206e6 + 140.023e6) / 288}
+NTT_FWD_DRAM_PER_LIMB = {"a": (151.169e6 + 95.007e6) / 288, "b": (246.732e6 + 137.494e6) / 345,
+                         "b_moddown": (450.748e6 + 143.621e6) / 288}
 
 
 # kernel variant those captures were taken on: traffic is reported only for it
-NTT_FWD_DRAM_VARIANT = 5
+NTT_FWD_DRAM_VARIANT = 6
 
 
 def traffic_source(dom, variant):

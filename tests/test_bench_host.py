@@ -31,7 +31,7 @@ def test_alu_microbench_summary():
 
 
 def test_traffic_only_for_the_captured_variant():
-    assert "variant 5, the tuner ran variant 4" in bench.traffic_source("ks_ntt_fwd", 4)
+    assert "variant 6, the tuner ran variant 4" in bench.traffic_source("ks_ntt_fwd", 4)
     assert bench.traffic_source("ks_ntt_fwd", bench.NTT_FWD_DRAM_VARIANT).startswith("ncu")
     assert bench.traffic_source("modup_bconv", 5).startswith("no DRAM")
 

@@ -34,7 +34,8 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
     // ModUp: coefficient representation of every input limb, then one base
     // conversion per digit and forward transforms of the new limbs
     gather_items(ctx, items, (size_t)coef_stride, d_in, coef, coef_stride);
-    ntt_inverse(ctx, Batch{coef, coef_stride, items, nullptr}, limb_range(0, ell, 0));
+    // n^{-1} of this transform is folded into the ModUp conversion's constants
+    ntt_inverse(ctx, Batch{coef, coef_stride, items, nullptr}, limb_range(0, ell, 0), false);
     modup_bconv(ctx, items, ell, coef, coef_stride, ext, ext_stride);
     ntt_forward(ctx, Batch{ext, ext_stride, items, nullptr}, modup_ntt_map(ctx, ell));
     ks_inner_product(ctx, items, ell, d_in, ext, ext_stride, groups, acc, acc_stride);
@@ -62,7 +63,7 @@ void rotate_hoisted(Ctx &ctx, const Keys &keys, int ell, const u64 *src, const s
     u64 *ext = rt.workspace(WS_HOIST_EXT, (size_t)ext_stride);
     const u64 *c1 = src + pstride;
     copy_words(ctx, coef, c1, (size_t)pstride);
-    ntt_inverse(ctx, Batch{coef, pstride, 1, nullptr}, limb_range(0, ell, 0));
+    ntt_inverse(ctx, Batch{coef, pstride, 1, nullptr}, limb_range(0, ell, 0), false);
     modup_bconv(ctx, 1, ell, coef, pstride, ext, ext_stride);
     ntt_forward(ctx, Batch{ext, ext_stride, 1, nullptr}, modup_ntt_map(ctx, ell));
     // per amount: inner product of the permuted extension, ModDown, c0 permuted

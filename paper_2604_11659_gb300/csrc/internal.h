@@ -49,12 +49,16 @@ struct DevTables {
     // hat_split[((hi-1)*alpha + i) * M + t] = (D/q_i mod m_t) * 2^64 mod m_t,
     // split into 30-bit halves (low half in the low word).
     u64 *mu_hat_inv = nullptr, *mu_hat_inv_p = nullptr, *mu_hat_split = nullptr;
+    // the same hat_inv times n^{-1} mod q_i (Shoup pairs): the conversion's
+    // inputs come from inverse transforms that leave out the n^{-1}
+    u64 *mu_hat_inv_n = nullptr, *mu_hat_inv_n_p = nullptr;
     // -D mod m_t in Montgomery form, split, with D = prod_{i in [lo, hi)} q_i: [(hi-1) * M + t]
     u64 *mu_negd_split = nullptr;
     double *inv_q = nullptr;                       // [M] 1 / m (correctly rounded double)
     // ModDown P -> Q: hat_inv over p_k, hat_split[k * M + i] (as above), and
     // P^{-1} mod q_i.
     u64 *md_hat_inv = nullptr, *md_hat_inv_p = nullptr, *md_hat_split = nullptr;
+    u64 *md_hat_inv_n = nullptr, *md_hat_inv_n_p = nullptr;   // times n^{-1} mod p_k
     u64 *md_pinv = nullptr, *md_pinv_p = nullptr;   // [L]
     u64 *md_negp_split = nullptr;                   // [L] -P mod q_i in Montgomery form, split
     // Rescale dropping q_t: rs_inv[t * L + i] = q_t^{-1} mod q_i (Shoup pair),

@@ -40,7 +40,10 @@ struct FuseArgs {
     const u64 *qt_mod = nullptr, *inv = nullptr, *invp = nullptr;
 };
 bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const FuseArgs &f);
-void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map);
+// scale = false leaves out the final factor n^{-1}: the limbs hold n x,
+// below 4q but not reduced (for the key-switching base conversions, whose
+// constants carry the n^{-1} instead)
+void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map, bool scale = true);
 LimbMap limb_range(int first_off, int count, int first_mi);
 
 // ---- ring kernels (ring.cu) ----

@@ -33,6 +33,10 @@ struct NttArgs {
     long long stride;
     const int *ids;
     LimbMap map;
+    // inverse transforms: 1 = leave out the final factor n^{-1} (the output is
+    // n x, not reduced below q; for consumers that fold n^{-1} into their own
+    // constants, the base conversions of key switching)
+    int unscaled = 0;
 };
 
 __device__ __forceinline__ u64 *limb_ptr(const NttArgs &a, int n, int &mi)
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_a(NttArgs a, const ModConst *_
     }
     for (int idx = threadIdx.x; idx < rows * C; idx += blockDim.x) {
         const int r = idx >> lgC, cc = idx & (C - 1);
-        p[((size_t)r << lg_ncols) + c0 + cc] = mul_shoup(sm[idx], m.n_inv, m.n_inv_p, q);
+        p[((size_t)r << lg_ncols) + c0 + cc] = a.unscaled ? sm[idx] : mul_shoup(sm[idx], m.n_inv, m.n_inv_p, q);
     }
 }
 
@@ -713,9 +717,14 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_a(NttArgs a,
         for (int i = 0; i < 16; ++i) v[i] = sm[r16_slot_a<P>(col, r16_index<P, 0>(t, i))];
         r16_inv_round<P, 0, false, false, AR>(v, t, w2, q, 0, 0);
     }
+    if (a.unscaled) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = mul_shoup(v[i], m.n_inv, m.n_inv_p, q);
+        for (int i = 0; i < 16; ++i) p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = v[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            p[((size_t)r16_index<P, 0>(t, i) << lg_ncols) + gcol] = mul_shoup(v[i], m.n_inv, m.n_inv_p, q);
+    }
 }
 
 // dynamic shared memory of pass B for variant V (opted in once per kernel and
@@ -1002,17 +1011,17 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
     return true;
 }
 
-void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map)
+void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map, bool scale)
 {
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return;
     Geometry g = geometry(ctx.log_n);
-    NttArgs a{b.base, b.stride, b.ids, map};
+    NttArgs a{b.base, b.stride, b.ids, map, scale ? 0 : 1};
     const int cls = ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV;
     if (ctx.log_n >= 12) {
         const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
         for_chunks(ctx, b, map, [&](const Batch &cb, const LimbMap &cm) {
-            NttArgs ca{cb.base, cb.stride, cb.ids, cm};
+            NttArgs ca{cb.base, cb.stride, cb.ids, cm, scale ? 0 : 1};
             dim3 grid(ctx.n / kElems, cm.nl, cb.items);
             {
                 cudaEvent_t t0_ = prof_begin(ctx);

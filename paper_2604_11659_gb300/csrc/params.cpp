@@ -215,6 +215,19 @@ void upload_tables(Ctx &ctx)
     t.mu_hat_inv = upload(hinv);
     t.mu_hat_inv_p = upload(hinvp);
     t.mu_hat_split = upload(hmont);
+    // hat_inv times n^{-1}: for inputs from inverse transforms that leave it out
+    std::vector<u64> hinvn(hinv.size()), hinvnp(hinv.size());
+    for (int hi = 1; hi <= L; ++hi) {
+        const int lo = ((hi - 1) / A) * A;
+        for (int i = lo; i < hi; ++i) {
+            const size_t row = (size_t)(hi - 1) * A + (i - lo);
+            const u64 qi = ctx.mods[i];
+            hinvn[row] = mulmod_host(hinv[row], ctx.mc[i].n_inv, qi);
+            hinvnp[row] = shoup_pre(hinvn[row], qi);
+        }
+    }
+    t.mu_hat_inv_n = upload(hinvn);
+    t.mu_hat_inv_n_p = upload(hinvnp);
 
     // ModDown P -> Q
     std::vector<u64> dinv(K), dinvp(K), dmont((size_t)K * M), pinv(L), pinvp(L), negp(L);
@@ -243,6 +256,14 @@ void upload_tables(Ctx &ctx)
     }
     t.md_hat_inv = upload(dinv);
     t.md_hat_inv_p = upload(dinvp);
+    std::vector<u64> dinvn(K), dinvnp(K);
+    for (int k = 0; k < K; ++k) {
+        const u64 pk = ctx.mods[L + k];
+        dinvn[k] = mulmod_host(dinv[k], ctx.mc[L + k].n_inv, pk);
+        dinvnp[k] = shoup_pre(dinvn[k], pk);
+    }
+    t.md_hat_inv_n = upload(dinvn);
+    t.md_hat_inv_n_p = upload(dinvnp);
     t.md_hat_split = upload(dmont);
     t.md_pinv = upload(pinv);
     t.md_pinv_p = upload(pinvp);
@@ -266,6 +287,7 @@ void free_tables(Ctx &ctx)
 {
     DevTables &t = ctx.dt;
     u64 *ptrs[] = {t.tw, t.twp, t.itw, t.itwp, t.mu_hat_inv, t.mu_hat_inv_p, t.mu_hat_split,
+                   t.mu_hat_inv_n, t.mu_hat_inv_n_p, t.md_hat_inv_n, t.md_hat_inv_n_p,
                    t.md_hat_inv, t.md_hat_inv_p, t.md_hat_split, t.md_pinv, t.md_pinv_p,
                    t.md_negp_split, t.mu_negd_split, t.rs_inv, t.rs_inv_p, t.rs_qt};
     for (u64 *p : ptrs)

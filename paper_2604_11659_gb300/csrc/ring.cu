@@ -680,7 +680,7 @@ void modup_bconv(Ctx &ctx, int items, int ell, const u64 *coef, long long coef_s
         ns_dispatch(ns, [&](auto NS) {
             k_modup_bconv<decltype(NS)::value><<<grid, kT, smem, ctx.stream>>>(
                 digit0, ell, ctx.L, ctx.K, ctx.alpha, ctx.M, ctx.n, coef, coef_stride, ext, ext_stride, ctx.dt.mc,
-                ctx.dt.mu_hat_inv, ctx.dt.mu_hat_inv_p, ctx.dt.mu_hat_split, ctx.dt.mu_negd_split, ctx.dt.inv_q);
+                ctx.dt.mu_hat_inv_n, ctx.dt.mu_hat_inv_n_p, ctx.dt.mu_hat_split, ctx.dt.mu_negd_split, ctx.dt.inv_q);
         });
         double macs = 0;
         for (int d = digit0; d < digit0 + ndig; ++d) macs += (double)ns * (ell + ctx.K - ns);
@@ -759,13 +759,14 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
             pm.off[b * ctx.K + k] = b * next + ell + k;
             pm.mi[b * ctx.K + k] = ctx.L + k;
         }
-    ntt_inverse(ctx, Batch{acc, acc_stride, items, nullptr}, pm);
+    // n^{-1} of this transform is folded into the conversion's constants
+    ntt_inverse(ctx, Batch{acc, acc_stride, items, nullptr}, pm, false);
     const size_t smem = (size_t)((ctx.K + 4) & ~1) * ell * sizeof(u64);
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         ns_dispatch(ctx.K, [&](auto KK) {
             k_moddown_bconv<decltype(KK)::value><<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
-                ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv, ctx.dt.md_hat_inv_p,
+                ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv_n, ctx.dt.md_hat_inv_n_p,
                 ctx.dt.md_hat_split, ctx.dt.md_negp_split, ctx.dt.inv_q);
         });
         prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");

@@ -72,6 +72,41 @@ def test_ntt_forward_inverse_bit_exact(log_n, q_bits, split, variant):
         p.close()
 
 
+@pytest.mark.parametrize("log_n,split", [(16, 0), (16, 7), (17, 0)])
+@pytest.mark.parametrize("variant", [5, 6])
+def test_ntt_many_limbs_bit_exact(log_n, split, variant):
+    """256 limbs in one launch (4096 to 8192 CTAs per pass, several waves of
+    resident CTAs, limbs of different moduli side by side, both butterfly
+    paths); limb l holds input row l mod 4 under modulus l mod 4, so every
+    limb is checked against one of the oracle's four transforms."""
+    sp = need_gpu()
+    import torch
+    recipe = synthetic.RingRecipe(log_n=log_n, q_bits=[60, 45, 59, 57], dnum=1, scale_bits=40)
+    p = Pair(recipe)
+    try:
+        sp.spfhe_ctx_set_ntt_split(p.ctx, split)
+        sp.spfhe_ctx_set_ntt_variant(p.ctx, variant)
+        n, M = p.n, p.M
+        rng = np.random.default_rng(100 + log_n)
+        x = np.stack([rng.integers(0, m, n, dtype=np.uint64) for m in p.P.mods])
+        x[2, :] = p.P.mods[2] - 1
+        want = p.o.rns_ntt(x, np.arange(M, dtype=np.int32))
+        nl = 256
+        mi = (np.arange(nl) % M).astype(np.int32)
+        xs = x[mi]
+        t = torch.from_numpy(xs.view(np.int64)).cuda()
+        sp.spfhe_ntt(p.ctx, t.data_ptr(), mi, inverse=False)
+        sp.spfhe_sync(p.ctx)
+        got = t.cpu().numpy().view(np.uint64)
+        bad = [l for l in range(nl) if not np.array_equal(got[l], want[mi[l]])]
+        assert not bad, "limbs differ from the oracle: %s" % bad[:8]
+        sp.spfhe_ntt(p.ctx, t.data_ptr(), mi, inverse=True)
+        sp.spfhe_sync(p.ctx)
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), xs)
+    finally:
+        p.close()
+
+
 def test_decrypt_bit_exact(pair):
     o, P = pair.o, pair.P
     rng = np.random.default_rng(1)

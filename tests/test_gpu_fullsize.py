@@ -87,6 +87,57 @@ def test_bench_workload_decrypts_within_tolerance():
         g.sp.spfhe_ctx_destroy(g.ctx)
 
 
+def test_bench_ring_launch_configurations_bit_identical():
+    """At the benchmark's ring with the library's own keys, a 128x128 product
+    with a few hundred matches (several 32-match batches and a ragged last
+    one) yields bit-identical result ciphertexts whatever the match batch (32,
+    the default; 7; 1, one match per launch sequence), the NTT kernel variant
+    (6, the default; 5; 0) and the epilogue fusion.  Every launch computes the
+    same integers by construction; this checks it at full size in the
+    benchmark's launch configuration, where the oracle is too slow to follow
+    every match (its exactness at this ring is the few-match test above).  The
+    result decrypts within 1e-4 of A B."""
+    import torch
+    import bench
+    rng = np.random.default_rng(7)
+    A = synthetic.bernoulli_sparse(rng, 128, 128, 0.985)
+    B = synthetic.bernoulli_sparse(rng, 128, 128, 0.985)
+    A = synthetic.rescale_rows_to_unit_output(A, B)
+    case = synthetic.MatmulCase("launch-configs", A, B, synthetic.ring_128x128())
+    g = bench.GpuMatmul(case, 256, torch.cuda.current_stream().cuda_stream, ntt_chunk=0, ntt_variant=6)
+    sp = g.sp
+
+    def run():
+        outs, st = g.step()
+        bits = [sp.spfhe_ct_export(g.ctx, h, g.n) for h in outs]
+        return outs, bits, st
+
+    try:
+        outs, ref, st = run()
+        assert st["matches"] > 3 * 32 and st["matches"] % 32 != 0
+        assert g.check(outs) < 1e-4
+        g.free(outs)
+        settings = [("match batch 7", lambda on: sp.spfhe_ctx_set_match_batch(g.ctx, 7 if on else 0)),
+                    ("match batch 1", lambda on: sp.spfhe_ctx_set_match_batch(g.ctx, 1 if on else 0)),
+                    ("NTT variant 5", lambda on: sp.spfhe_ctx_set_ntt_variant(g.ctx, 5 if on else 6)),
+                    ("NTT variant 0", lambda on: sp.spfhe_ctx_set_ntt_variant(g.ctx, 0 if on else 6)),
+                    ("fusion off", lambda on: sp.spfhe_ctx_set_fusion(g.ctx, not on))]
+        for name, apply in settings:
+            apply(True)
+            try:
+                outs, bits, st2 = run()
+                g.free(outs)
+            finally:
+                apply(False)
+            assert st2["matches"] == st["matches"], name
+            assert all(np.array_equal(a, b) for a, b in zip(bits, ref)), name
+    finally:
+        sp.spfhe_keys_free(g.keys)
+        for h in g.A_cts + g.B_cts:
+            sp.spfhe_ct_free(h)
+        sp.spfhe_ctx_destroy(g.ctx)
+
+
 def _dense_layer_few_matches():
     """64x784 activations times 784x128 weights at the dense layer's ring with
     three matches: (0, 0) aligns A by 2 slots and needs no final rotation,

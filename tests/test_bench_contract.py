@@ -122,6 +122,7 @@ def stubbed(monkeypatch):
     monkeypatch.setattr(bench, "serve_run", lambda *a, **k: {"served": {"p99_ms": 1.0}})
     monkeypatch.setattr(bench, "dense_layer_pt", lambda *a, **k: {"ms": 1.0})
     monkeypatch.setattr(bench, "naive_sweep", lambda *a, **k: {"rows": []})
+    monkeypatch.setattr(bench, "accuracy_table2", lambda *a, **k: {"rows": []})
     monkeypatch.setattr(bench, "workload_16x16_end_to_end", lambda *a, **k: {"gpu_ms": 1.0})
     monkeypatch.setattr(bench, "cpu_baseline_line", lambda *a, **k: {"value": 2e-5, "unit": "matmuls/s",
                                                                       "cores": 8, "kind": "oracle", "sample": "s"})
@@ -164,7 +165,8 @@ def test_default_line_carries_the_contract(stubbed, monkeypatch, capsys):
                                      "tuner_key_gib": pytest.approx(37251710976 / 2 ** 30)}
     assert line["graph"]["vs_eager"] == pytest.approx(1.0)
     assert line["variant_grouped"]["ks_per_step"] == 11403 + 3003 + 11423
-    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "naive_sweep_16x16", "workload_16x16"):
+    for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "naive_sweep_16x16", "accuracy_table2",
+              "workload_16x16"):
         assert k in line
 
 
@@ -175,7 +177,7 @@ def test_skips_leave_their_keys_out(stubbed, monkeypatch, capsys):
                                       "--no-cpu-baseline"])
     assert line["graph"] is None and line["variant_grouped"] is None
     for k in ("batch", "batch_128x128", "serve", "dense_layer_ct_pt", "cpu_baseline", "naive_sweep_16x16",
-              "workload_16x16"):
+              "accuracy_table2", "workload_16x16"):
         assert k not in line
     assert line["ms_per_step"] == pytest.approx(STEP_MS)
 
@@ -220,6 +222,7 @@ def _install_stubs(rank):
     bench.serve_run = lambda *a, **k: {"served": {"p99_ms": 1.0}}
     bench.dense_layer_pt = lambda *a, **k: {"ms": 1.0}
     bench.naive_sweep = lambda *a, **k: {"rows": []}
+    bench.accuracy_table2 = lambda *a, **k: {"rows": []}
 
 
 def _bench_rank(rank, world, port, out_dir):

@@ -10,10 +10,23 @@ namespace spfhe {
 
 static int beta_of(const Ctx &ctx, int ell) { return (ell + ctx.alpha - 1) / ctx.alpha; }
 
-void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
-                     const u64 *const *d_base, const int *d_base_g, bool base_c1, u64 *out, long long out_stride)
+namespace {
+// Marks the launches of a key switch (their transforms are profiled apart).
+struct InKeySwitch {
+    Ctx &c;
+    explicit InKeySwitch(Ctx &x) : c(x) { ++c.in_keyswitch; }
+    ~InKeySwitch() { --c.in_keyswitch; }
+};
+
+struct KsBuffers {
+    u64 *acc, *conv;
+    long long acc_stride;
+};
+
+// ModUp and the inner product of a key-switching batch: acc [items][2][ell+K][n]
+// (evaluation rep.) and the workspace for ModDown's conversion.
+KsBuffers ks_front(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups)
 {
-    if (items <= 0) return;
     Runtime &rt = *ctx.rt;
     const size_t n = ctx.n;
     const int next = ell + ctx.K, beta = beta_of(ctx, ell);
@@ -24,11 +37,6 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
     u64 *ext = rt.workspace(WS_KS_EXT, (size_t)items * ext_stride);
     u64 *acc = rt.workspace(WS_KS_ACC, (size_t)items * acc_stride);
     u64 *conv = rt.workspace(WS_KS_CONV, (size_t)items * 2 * ell * n);
-    struct InKs {
-        Ctx &c;
-        explicit InKs(Ctx &x) : c(x) { ++c.in_keyswitch; }
-        ~InKs() { --c.in_keyswitch; }
-    } in_ks(ctx);
     ctx.prof.ks_calls += items;
     ctx.prof.ks_bytes += 8.0 * n * (3.0 * ell * items + 2.0 * beta * next * groups.size());
     // ModUp: coefficient representation of every input limb, then one base
@@ -39,7 +47,90 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
     modup_bconv(ctx, items, ell, coef, coef_stride, ext, ext_stride);
     ntt_forward(ctx, Batch{ext, ext_stride, items, nullptr}, modup_ntt_map(ctx, ell));
     ks_inner_product(ctx, items, ell, d_in, ext, ext_stride, groups, acc, acc_stride);
-    moddown(ctx, items, ell, acc, acc_stride, conv, d_base, d_base_g, base_c1, out, out_stride);
+    return KsBuffers{acc, conv, acc_stride};
+}
+}  // namespace
+
+void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
+                     const u64 *const *d_base, const int *d_base_g, bool base_c1, u64 *out, long long out_stride)
+{
+    if (items <= 0) return;
+    InKeySwitch in_ks(ctx);
+    const KsBuffers kb = ks_front(ctx, items, ell, d_in, groups);
+    moddown(ctx, items, ell, kb.acc, kb.acc_stride, kb.conv, d_base, d_base_g, base_c1, out, out_stride);
+}
+
+bool relin_rescale_supported(const Ctx &ctx, int ell)
+{
+    return ctx.fuse_epilogues && ctx.log_n >= 12 && (ctx.ntt_variant == 5 || ctx.ntt_variant == 6) && ell >= 2;
+}
+
+// Relinearisation followed by a rescale (Alg. 2's Relinearize, then
+// Rescale) with one transform per output limb instead of two.  ModDown's
+// output is o_b[i] = base_b[i] + P^{-1} (acc_b[i] - NTT(conv_b[i])) and the
+// rescale turns it into (o_b[i] - NTT([t_b]_{q_i})) q_t^{-1}, t_b the
+// coefficients of o_b's top limb.  The transform is linear over Z_{q_i}, so
+// (P^{-1} acc_b[i] + base_b[i] - NTT(P^{-1} conv_b[i] + [t_b]_{q_i})) q_t^{-1}
+// is the same residue: ModDown's own transforms of conv are left out, and
+// t_b = P^{-1} (INTT(acc_b[t]) - conv_b[t]) + INTT(base_b[t]) comes from two
+// inverse transforms of top limbs instead of one.
+void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
+                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride)
+{
+    if (items <= 0) return;
+    if (!relin_rescale_supported(ctx, ell)) throw Error(SPFHE_EINVAL, "merged relinearise-rescale unavailable");
+    const size_t n = ctx.n;
+    const int next = ell + ctx.K;
+    KsBuffers kb;
+    {
+        InKeySwitch in_ks(ctx);
+        kb = ks_front(ctx, items, ell, d_in, groups);
+        moddown_conv(ctx, items, ell, kb.acc, kb.acc_stride, kb.conv);
+    }
+    // tmp: top limbs [items][2][n], then the spread buffer [items][2][ell-1][n]
+    u64 *top = tmp;
+    u64 *spread = tmp + (size_t)items * 2 * n;
+    copy_top(ctx, items, ell, 2, d_base, top);
+    LimbMap tm;
+    tm.nl = 2;
+    tm.off[0] = 0;
+    tm.off[1] = 1;
+    tm.mi[0] = tm.mi[1] = ell - 1;
+    ntt_inverse(ctx, Batch{top, 2LL * (long long)n, items, nullptr}, tm);
+    LimbMap am;
+    am.nl = 2;
+    am.off[0] = ell - 1;
+    am.off[1] = next + ell - 1;
+    am.mi[0] = am.mi[1] = ell - 1;
+    ntt_inverse(ctx, Batch{kb.acc, kb.acc_stride, items, nullptr}, am);
+    relin_top(ctx, items, ell, kb.acc, kb.acc_stride, kb.conv, top);
+    LimbMap sm;
+    sm.nl = 2 * (ell - 1);
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < ell - 1; ++i) {
+            sm.off[b * (ell - 1) + i] = b * (ell - 1) + i;
+            sm.mi[b * (ell - 1) + i] = i;
+        }
+    FuseArgs fa;
+    fa.ell = ell;
+    fa.K = ctx.K;
+    fa.polys = 2;
+    fa.top = top;
+    fa.conv = kb.conv;
+    fa.conv_stride = 2LL * ell * n;
+    fa.acc = kb.acc;
+    fa.acc_stride = kb.acc_stride;
+    fa.base = d_base;
+    fa.out = out;
+    fa.out_stride = out_stride;
+    fa.pinv = ctx.dt.md_pinv;
+    fa.pinvp = ctx.dt.md_pinv_p;
+    fa.qt_mod = ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L;
+    fa.inv = ctx.dt.rs_inv + (size_t)(ell - 1) * ctx.L;
+    fa.invp = ctx.dt.rs_inv_p + (size_t)(ell - 1) * ctx.L;
+    if (!ntt_forward_fused(ctx, Batch{spread, 2LL * (ell - 1) * (long long)n, items, nullptr}, sm, kFuseRelinRescale,
+                           fa))
+        throw Error(SPFHE_EINVAL, "merged relinearise-rescale transform refused");
 }
 
 void rotate_hoisted(Ctx &ctx, const Keys &keys, int ell, const u64 *src, const std::vector<int> &amounts, u64 *out)

@@ -560,9 +560,14 @@ void spmspm_ct_ct_grouped(Ctx &ctx, const Keys &keys, const spfhe_sparse_meta &A
                 std::vector<KeyGroup> kg;
                 for (int g = 0; g < k; g += kRelinShare)
                     kg.push_back(KeyGroup{keys.relin, g, std::min(kRelinShare, k - g)});
-                keyswitch_batch(ctx, k, ell - 1, rt.upload_vec(d2), kg, rt.upload_vec(base), nullptr, true, R2, cs1);
+                if (relin_rescale_supported(ctx, ell - 1)) {
+                    relin_rescale_batch(ctx, k, ell - 1, rt.upload_vec(d2), kg, rt.upload_vec(base), T, X, cs2);
+                } else {
+                    keyswitch_batch(ctx, k, ell - 1, rt.upload_vec(d2), kg, rt.upload_vec(base), nullptr, true, R2,
+                                    cs1);
+                    rescale(ctx, k, ell - 1, rt.upload_vec(x1), T, X, cs2, 2);
+                }
                 st_relin += k;
-                rescale(ctx, k, ell - 1, rt.upload_vec(x1), T, X, cs2, 2);
                 st_rescales += 2ull * k;
                 tree.push(key, x2, ge < gl.size() ? gl[ge]->first : Key{INT_MAX, 0});
             }

@@ -25,12 +25,22 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map);
 //   kFuseRescale: pass A reads [r]_{q_i} from the centred top limbs
 //     (top [items][polys][n]) instead of a spread buffer, pass B writes
 //     out = (in - [r]_{q_i}) q_t^{-1}; the batch is the spread buffer
-//     [items][polys][ell-1][n] that holds the intermediate pass.
-enum { kFuseNone = 0, kFuseModDown = 1, kFuseRescale = 2 };
+//     [items][polys][ell-1][n] that holds the intermediate pass;
+//   kFuseRelinRescale (variants 5 and 6 only): ModDown's last step and the
+//     rescale that follows it in one transform (relin_rescale_batch): pass A
+//     reads P^{-1} conv_b[i] + [t_b]_{q_i} (conv [items][2][ell][n]
+//     coefficient rep., t_b the relinearised top limb's coefficients, top
+//     [items][2][n]), pass B writes
+//     out = (P^{-1} acc_b[i] + base_b[i] - X) q_t^{-1}, X the transform.
+//     By linearity of the transform this is, residue for residue, ModDown's
+//     output rescaled: the transform of conv and the one of [t]_{q_i} are
+//     taken together.
+enum { kFuseNone = 0, kFuseModDown = 1, kFuseRescale = 2, kFuseRelinRescale = 3 };
 struct FuseArgs {
     int ell = 0, K = 0, polys = 0, base_c1 = 0;
     const u64 *acc = nullptr;
-    long long acc_stride = 0, out_stride = 0;
+    const u64 *conv = nullptr;
+    long long acc_stride = 0, out_stride = 0, conv_stride = 0;
     const u64 *const *base = nullptr;
     const int *base_g = nullptr;
     u64 *out = nullptr;
@@ -83,6 +93,16 @@ void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const 
 // base: per item [2][ell][n] (or nullptr), read at sigma_g index when g given.
 void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv,
              const u64 *const *base, const int *base_g, bool base_c1, u64 *out, long long out_stride);
+// ModDown's first half: the P limbs of acc inverse transformed in place and
+// converted into conv [items][2][ell][n] (coefficient rep.).
+void moddown_conv(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv);
+// Coefficients of the relinearised ciphertext's top limb (modulus q_{ell-1}):
+// top[item][b] = (acc_b[ell-1] - conv_b[ell-1]) P^{-1} + base_b[ell-1], with
+// acc's top limbs and base's top limbs (top [items][2][n] on entry) already
+// in coefficient rep.
+void relin_top(Ctx &ctx, int items, int ell, const u64 *acc, long long acc_stride, const u64 *conv, u64 *top);
+// k_copy_top: top[item][b] = in[item][b][ell-1] for b < polys
+void copy_top(Ctx &ctx, int items, int ell, int polys, const u64 *const *in, u64 *top);
 
 // Rescale every item [polys][ell][n] -> out [polys][ell-1][n] (polys 1..3);
 // tmp holds items * polys * ell * n words.

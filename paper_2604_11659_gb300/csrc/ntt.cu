@@ -381,6 +381,8 @@ template <int P> constexpr int r16_smem_words_b() { return kElems + (kElems >> 4
 template <int V> constexpr int r16_min_blocks() { return V == 0 ? 3 : (V >= 3 ? 4 : 2); }
 template <int V> constexpr int r16_arith() { return V >= 5 ? 2 : (V == 4 ? 1 : 0); }
 template <int V> constexpr bool r16_warp_local() { return V == 6; }
+// variants that carry the merged relinearise-rescale transform (kFuseRelinRescale)
+template <int V> constexpr bool r16_relin_rescale() { return V == 5 || V == 6; }
 
 // Pass B, V = 2: start the asynchronous copy of the CTA's twiddles.
 template <int P>
@@ -432,7 +434,7 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
     const int col = threadIdx.x % TPC, t = threadIdx.x / TPC;
     const int gcol = blockIdx.x * TPC + col;
     u64 v[16];
-    if constexpr (MODE == kFuseRescale) {
+    if constexpr (MODE == kFuseRescale || MODE == kFuseRelinRescale) {
         // the limb [r]_{q_i} of the centred top limb r, read from the top limb itself
         const int slot = blockIdx.y, it = blockIdx.z;
         const int b = slot / (f.ell - 1), i = slot % (f.ell - 1);
@@ -445,6 +447,15 @@ __device__ __forceinline__ void fwd16_a_body(u64 *sm, u64 *p, u64 q, const ulong
             u64 r = mul_shoup(redc(U128{c, 0}, m.q, m.qneg_inv), m.r_mod, m.r_mod_p, m.q);
             if (c > qt_half) r = sub_mod(r, qt_mod, m.q);
             v[x] = r;
+        }
+        if constexpr (MODE == kFuseRelinRescale) {
+            // plus P^{-1} times ModDown's conversion of limb i (coefficient rep.)
+            const u64 *cv = f.conv + it * f.conv_stride + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+            const u64 pinv = __ldg(f.pinv + i), pinvp = __ldg(f.pinvp + i);
+#pragma unroll
+            for (int x = 0; x < 16; ++x)
+                v[x] = add_mod(v[x], mul_shoup(cv[((size_t)r16_index<P, 0>(t, x) << lg_ncols) + gcol], pinv, pinvp, m.q),
+                               m.q);
         }
     } else {
 #pragma unroll
@@ -561,6 +572,34 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
                 u64 v = mul_shoup(sub_mod(av[r], c, q), pinv, pinvp, q);
                 if (add_base) v = add_mod(v, bv[r], q);
                 out[e0 + x] = v;
+            }
+        }
+    } else if constexpr (MODE == kFuseRelinRescale) {
+        // out_b[i] = (P^{-1} acc_b[i] + base_b[i] - X) q_t^{-1}, X = this
+        // transform of P^{-1} conv_b[i] + [t_b]_{q_i}: ModDown's output
+        // rescaled, by linearity of the transform
+        const int slot = blockIdx.y, it = blockIdx.z;
+        const int b = slot / (f.ell - 1), i = slot % (f.ell - 1);
+        const int next = f.ell + f.K;
+        const u64 pinv = __ldg(f.pinv + i), pinvp = __ldg(f.pinvp + i);
+        const u64 inv = __ldg(f.inv + i), invp = __ldg(f.invp + i);
+        const u64 *__restrict__ acc = f.acc + it * f.acc_stride + ((size_t)b * next + i) * ((size_t)1 << log_n);
+        const u64 *__restrict__ base = f.base[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
+        u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
+        for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
+            u64 av[8], bv[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const size_t k = e0 + x0 + r * r16_step<WL>();
+                av[r] = acc[k];
+                bv[r] = base[k];
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int x = x0 + r * r16_step<WL>();
+                const u64 X = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+                const u64 y = add_mod(mul_shoup(av[r], pinv, pinvp, q), bv[r], q);
+                out[e0 + x] = mul_shoup(sub_mod(y, X, q), inv, invp, q);
             }
         }
     } else {
@@ -776,12 +815,20 @@ template <int P, int V> struct R16FusedV {
     static void fwd_a(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int mode, const FuseArgs &f)
     {
         if (mode == kFuseRescale) k_fwd16_a<P, V, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
-        else k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+        else if (mode == kFuseRelinRescale) {
+            if constexpr (r16_relin_rescale<V>())
+                k_fwd16_a<P, V, kFuseRelinRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
+            else throw Error(SPFHE_EINVAL, "no merged relinearise-rescale transform for this NTT variant");
+        } else k_fwd16_a<P, V><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, f);
     }
     static void fwd_b(dim3 g, cudaStream_t s, const NttArgs &a, const Ctx &c, int PA, int mode, const FuseArgs &f)
     {
         if (mode == kFuseRescale) k_fwd16_b<P, V, kFuseRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
-        else k_fwd16_b<P, V, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+        else if (mode == kFuseRelinRescale) {
+            if constexpr (r16_relin_rescale<V>())
+                k_fwd16_b<P, V, kFuseRelinRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+            else throw Error(SPFHE_EINVAL, "no merged relinearise-rescale transform for this NTT variant");
+        } else k_fwd16_b<P, V, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
     }
 };
 template <int P> struct R16Fused {
@@ -981,6 +1028,7 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
 {
     if (ctx.log_n < 12 || ctx.ntt_variant == 1 || ctx.ntt_variant == 2 || b.ids)
         return false;
+    if (mode == kFuseRelinRescale && ctx.ntt_variant != 5 && ctx.ntt_variant != 6) return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
     NttArgs a{b.base, b.stride, b.ids, map};
@@ -990,8 +1038,11 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
     {
         cudaEvent_t t0_ = prof_begin(ctx);
         r16_fused_dispatch(PA, [&](auto L) { decltype(L)::fwd_a(grid, ctx.stream, a, ctx, mode, f); });
-        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * PA * map.nl * b.items,
-                 mode == kFuseRescale ? "ntt fwd A + rescale spread" : "ntt fwd A");
+        // the merged relinearise-rescale pass also reads ModDown's conversion
+        prof_end(ctx, t0_, cls, (mode == kFuseRelinRescale ? 16.0 : 8.0) * ctx.n * map.nl * b.items,
+                 0.5 * ctx.n * PA * map.nl * b.items,
+                 mode == kFuseRescale ? "ntt fwd A + rescale spread"
+                 : mode == kFuseRelinRescale ? "ntt fwd A + relinearised spread" : "ntt fwd A");
         prof_limbs(ctx, cls, 0, (double)map.nl * b.items);
     }
     {
@@ -1001,11 +1052,13 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
         // polynomials, or only c0 for a rotation) and writes out; the rescale
         // reads its input limb and writes out
         const double base_limbs = !f.base ? 0.0 : (f.base_c1 ? 1.0 : 0.5) * map.nl;
-        const double epi = mode == kFuseModDown ? 16.0 * ctx.n * map.nl + 8.0 * ctx.n * base_limbs
-                                                : 16.0 * ctx.n * map.nl;
+        const double epi = mode == kFuseModDown        ? 16.0 * ctx.n * map.nl + 8.0 * ctx.n * base_limbs
+                           : mode == kFuseRelinRescale ? 24.0 * ctx.n * map.nl
+                                                       : 16.0 * ctx.n * map.nl;
         prof_end(ctx, t0_, cls, epi * b.items,
                  0.5 * ctx.n * PB * map.nl * b.items,
-                 mode == kFuseRescale ? "ntt fwd B + rescale final" : "ntt fwd B + moddown final");
+                 mode == kFuseRescale ? "ntt fwd B + rescale final"
+                 : mode == kFuseRelinRescale ? "ntt fwd B + relinearise-rescale final" : "ntt fwd B + moddown final");
         prof_limbs(ctx, cls, 2, (double)map.nl * b.items);
     }
     return true;

@@ -358,6 +358,23 @@ __global__ void k_copy_top(int polys, int ell, int n, const u64 *const *in, u64 
     top[((size_t)it * polys + b) * n + k] = in[it][((size_t)b * ell + ell - 1) * n + k];
 }
 
+// Relinearised top limb in coefficient rep. (modulus q_t = q_{ell-1}):
+// top[it][b] = [(acc_b[t] - conv_b[t]) P^{-1} + top[it][b]]_{q_t}, with
+// acc_b[t] and the base's top limb (top on entry) already inverse transformed.
+__global__ void k_relin_top(int ell, int K, int n, const u64 *acc, long long acc_stride, const u64 *conv, u64 *top,
+                            const ModConst *__restrict__ mc, const u64 *__restrict__ pinv,
+                            const u64 *__restrict__ pinvp)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int b = blockIdx.y, it = blockIdx.z, t = ell - 1;
+    const u64 q = mc[t].q;
+    const u64 a = acc[it * acc_stride + ((size_t)b * (ell + K) + t) * n + k];
+    const u64 c = conv[((size_t)it * 2 + b) * ell * n + (size_t)t * n + k];
+    u64 *o = top + ((size_t)it * 2 + b) * n + k;
+    *o = add_mod(mul_shoup(sub_mod(a, c, q), __ldg(pinv + t), __ldg(pinvp + t), q), *o, q);
+}
+
 __global__ void k_mul_plain_perm(int ell, int log_n, u64 *ct, long long stride, const u64 *const *mask, const int *g,
                                  const ModConst *__restrict__ mc)
 {
@@ -750,27 +767,7 @@ void ks_inner_product(Ctx &ctx, int items, int ell, const u64 *const *in, const 
 void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv, const u64 *const *base,
              const int *base_g, bool base_c1, u64 *out, long long out_stride)
 {
-    const int next = ell + ctx.K;
-    // inverse NTT of the P limbs of both accumulators
-    LimbMap pm;
-    pm.nl = 2 * ctx.K;
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < ctx.K; ++k) {
-            pm.off[b * ctx.K + k] = b * next + ell + k;
-            pm.mi[b * ctx.K + k] = ctx.L + k;
-        }
-    // n^{-1} of this transform is folded into the conversion's constants
-    ntt_inverse(ctx, Batch{acc, acc_stride, items, nullptr}, pm, false);
-    const size_t smem = (size_t)((ctx.K + 4) & ~1) * ell * sizeof(u64);
-    {
-        cudaEvent_t t0_ = prof_begin(ctx);
-        ns_dispatch(ctx.K, [&](auto KK) {
-            k_moddown_bconv<decltype(KK)::value><<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
-                ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv_n, ctx.dt.md_hat_inv_n_p,
-                ctx.dt.md_hat_split, ctx.dt.md_negp_split, ctx.dt.inv_q);
-        });
-        prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");
-    }
+    moddown_conv(ctx, items, ell, acc, acc_stride, conv);
     LimbMap qm;
     qm.nl = 2 * ell;
     for (int b = 0; b < 2; ++b)
@@ -803,6 +800,50 @@ void moddown(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *
     }
 }
 
+void moddown_conv(Ctx &ctx, int items, int ell, u64 *acc, long long acc_stride, u64 *conv)
+{
+    const int next = ell + ctx.K;
+    // inverse NTT of the P limbs of both accumulators
+    LimbMap pm;
+    pm.nl = 2 * ctx.K;
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < ctx.K; ++k) {
+            pm.off[b * ctx.K + k] = b * next + ell + k;
+            pm.mi[b * ctx.K + k] = ctx.L + k;
+        }
+    // n^{-1} of this transform is folded into the conversion's constants
+    ntt_inverse(ctx, Batch{acc, acc_stride, items, nullptr}, pm, false);
+    const size_t smem = (size_t)((ctx.K + 4) & ~1) * ell * sizeof(u64);
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        ns_dispatch(ctx.K, [&](auto KK) {
+            k_moddown_bconv<decltype(KK)::value><<<grid_n(ctx.n, 2, items), kT, smem, ctx.stream>>>(
+                ell, ctx.L, ctx.M, ctx.n, acc, acc_stride, conv, ctx.dt.mc, ctx.dt.md_hat_inv_n, ctx.dt.md_hat_inv_n_p,
+                ctx.dt.md_hat_split, ctx.dt.md_negp_split, ctx.dt.inv_q);
+        });
+        prof_end(ctx, t0_, K_MODDOWN_BCONV, 16.0 * ctx.n * items * (ctx.K + ell), 2.0 * ctx.n * items * ctx.K * ell, "moddown bconv");
+    }
+}
+
+void relin_top(Ctx &ctx, int items, int ell, const u64 *acc, long long acc_stride, const u64 *conv, u64 *top)
+{
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_relin_top<<<grid_n(ctx.n, 2, items), kT, 0, ctx.stream>>>(ell, ctx.K, ctx.n, acc, acc_stride, conv, top,
+                                                                   ctx.dt.mc, ctx.dt.md_pinv, ctx.dt.md_pinv_p);
+        prof_end(ctx, t0_, K_RESCALE, 32.0 * ctx.n * items * 2, 2.0 * ctx.n * items, "relinearised top limb");
+    }
+}
+
+void copy_top(Ctx &ctx, int items, int ell, int polys, const u64 *const *in, u64 *top)
+{
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        k_copy_top<<<grid_n(ctx.n, polys, items), kT, 0, ctx.stream>>>(polys, ell, ctx.n, in, top);
+        prof_end(ctx, t0_, K_RESCALE, 16.0 * ctx.n * items * polys, 0.0, "rescale copy");
+    }
+}
+
 void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *out, long long out_stride, int polys)
 {
     if (ell < 2) throw Error(SPFHE_ELEVEL, "rescale needs two limbs");
@@ -811,11 +852,7 @@ void rescale(Ctx &ctx, int items, int ell, const u64 *const *in, u64 *tmp, u64 *
     // tmp layout: [items][polys][n] top limbs, then [items][polys][ell-1][n]
     u64 *top = tmp;
     u64 *spread = tmp + (size_t)items * polys * n;
-    {
-        cudaEvent_t t0_ = prof_begin(ctx);
-        k_copy_top<<<grid_n(n, polys, items), kT, 0, ctx.stream>>>(polys, ell, n, in, top);
-        prof_end(ctx, t0_, K_RESCALE, 16.0 * n * items * polys, 0.0, "rescale copy");
-    }
+    copy_top(ctx, items, ell, polys, in, top);
     LimbMap tm;
     tm.nl = polys;
     for (int b = 0; b < polys; ++b) {

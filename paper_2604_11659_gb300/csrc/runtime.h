@@ -58,6 +58,16 @@ enum WsSlot {
 void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
                      const u64 *const *d_base, const int *d_base_g, bool base_c1, u64 *out, long long out_stride);
 
+// Relinearisation of d_in (the tensor's d2, [ell][n] per item) added to the
+// base d_base ((d0, d1), [2][ell][n] per item), then rescaled: out
+// [items][2][ell-1][n], bit for bit keyswitch_batch followed by rescale, with
+// one forward transform per output limb (ModDown's are folded into the
+// rescale's; see ckks.cpp).  tmp holds items * 2 * ell * n words.  Needs
+// relin_rescale_supported (fused epilogues, n >= 2^12, NTT variant 5 or 6).
+bool relin_rescale_supported(const Ctx &ctx, int ell);
+void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
+                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride);
+
 // One rotation step per item: item i of `in` ([2][ell][n]) rotated with
 // Galois element g[i] and key keys[i]; out [items][2][ell][n].
 void rotate_step_batch(Ctx &ctx, int ell, const std::vector<const u64 *> &in, const std::vector<int> &g,

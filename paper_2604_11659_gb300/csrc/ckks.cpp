@@ -2,6 +2,7 @@
 // rotation plan, key generation and encryption, all sequenced on the
 // context's stream.
 #include <algorithm>
+#include <map>
 #include <numeric>
 
 #include "runtime.h"
@@ -131,6 +132,169 @@ void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, c
     if (!ntt_forward_fused(ctx, Batch{spread, 2LL * (ell - 1) * (long long)n, items, nullptr}, sm, kFuseRelinRescale,
                            fa))
         throw Error(SPFHE_EINVAL, "merged relinearise-rescale transform refused");
+}
+
+bool rotate_accumulate_supported(const Ctx &ctx)
+{
+    return ctx.fuse_epilogues && ctx.log_n >= 12 && (ctx.ntt_variant == 5 || ctx.ntt_variant == 6);
+}
+
+// Rotations through the plan whose results are only summed into result
+// ciphertexts (Alg. 2's EvalRotate then EvalAdd).  Every step but the last
+// runs as in rotate_batch.  The last step's ModDown output is
+// sigma_g(c0) + P^{-1} (acc - NTT(conv)) (c1's part without sigma_g(c0));
+// summed over the sources of one result ciphertext that is
+// sum sigma_g(c0) + P^{-1} (sum acc - NTT(sum conv)), the transform being
+// linear over Z_q: one forward transform per result ciphertext and batch
+// instead of one per source, and no rotated ciphertext written out.  The
+// sums are exact residues, so the result is bit for bit rotate_batch's
+// outputs added into the targets.
+void rotate_accumulate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell,
+                             const std::vector<const u64 *> &in, const std::vector<int> &r,
+                             const std::vector<u64 *> &tgt, uint64_t *ks)
+{
+    if (!rotate_accumulate_supported(ctx)) throw Error(SPFHE_EINVAL, "fused rotate-accumulate unavailable");
+    Runtime &rt = *ctx.rt;
+    const int items = (int)in.size();
+    if (!items) return;
+    const size_t n = ctx.n;
+    const long long pstride = (long long)ell * n, cstride = 2 * pstride;
+    std::vector<std::vector<int>> plans(items);
+    size_t T = 0;
+    for (int i = 0; i < items; ++i) {
+        plans[i] = rotation_plan(ctx, r[i]);
+        T = std::max(T, plans[i].size());
+        for (int a : plans[i]) rotation_key(*keys[i], a);   // EKEY before any launch
+    }
+    // every step but each item's last; an item whose prefix ends while more
+    // prefix steps follow is copied aside (the step buffers alternate)
+    std::vector<const u64 *> cur(in.begin(), in.end());
+    u64 *buf[2] = {rt.workspace(WS_ROT_OUT_A, (size_t)items * cstride),
+                   rt.workspace(WS_ROT_OUT_B, (size_t)items * cstride)};
+    u64 *hold = T > 3 ? rt.workspace(WS_MISC, (size_t)items * cstride) : nullptr;
+    for (size_t s = 0; s + 1 < T; ++s) {
+        std::vector<int> act;
+        for (int i = 0; i < items; ++i)
+            if (plans[i].size() > s + 1) act.push_back(i);
+        std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
+            return rotation_key(*keys[a], plans[a][s]) < rotation_key(*keys[b], plans[b][s]);
+        });
+        std::vector<const u64 *> sin, skey;
+        std::vector<int> sg;
+        for (int i : act) {
+            sin.push_back(cur[i]);
+            sg.push_back(galois_element(ctx, plans[i][s]));
+            skey.push_back(rotation_key(*keys[i], plans[i][s]));
+        }
+        u64 *dst = buf[s & 1];
+        rotate_step_batch(ctx, ell, sin, sg, skey, dst);
+        if (ks) *ks += act.size();
+        std::vector<const u64 *> keep_src;
+        std::vector<u64 *> keep_dst;
+        for (size_t k = 0; k < act.size(); ++k) {
+            const int i = act[k];
+            cur[i] = dst + k * cstride;
+            // its prefix ends here; step s + 2 (if any) writes this buffer again
+            if (plans[i].size() == s + 2 && s + 3 < T) {
+                keep_src.push_back(cur[i]);
+                keep_dst.push_back(hold + i * cstride);
+                cur[i] = hold + i * cstride;
+            }
+        }
+        for (size_t k = 0; k < keep_src.size(); ++k) copy_words(ctx, keep_dst[k], keep_src[k], (size_t)cstride);
+    }
+    // the last step of every rotated item, keys grouped
+    std::vector<int> act;
+    for (int i = 0; i < items; ++i)
+        if (!plans[i].empty()) act.push_back(i);
+    std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
+        return rotation_key(*keys[a], plans[a].back()) < rotation_key(*keys[b], plans[b].back());
+    });
+    const int A = (int)act.size();
+    if (A) {
+        std::vector<const u64 *> c1(A), tp(A);
+        std::vector<int> g(A);
+        std::vector<KeyGroup> groups;
+        u64 *tmp = rt.workspace(WS_ROT_TMP, (size_t)A * pstride);
+        for (int k = 0; k < A; ++k) {
+            const int i = act[k];
+            c1[k] = cur[i] + pstride;
+            tp[k] = tmp + k * pstride;
+            g[k] = galois_element(ctx, plans[i].back());
+            const u64 *key = rotation_key(*keys[i], plans[i].back());
+            if (!groups.empty() && groups.back().key == key)
+                ++groups.back().count;
+            else
+                groups.push_back(KeyGroup{key, k, 1});
+        }
+        automorph(ctx, A, 1, ell, rt.upload_vec(c1), 0, tmp, pstride, rt.upload_vec(g));
+        KsBuffers kb;
+        {
+            InKeySwitch in_ks(ctx);
+            kb = ks_front(ctx, A, ell, rt.upload_vec(tp), groups);
+            moddown_conv(ctx, A, ell, kb.acc, kb.acc_stride, kb.conv);
+        }
+        if (ks) *ks += A;
+        // sources by target
+        std::map<u64 *, std::vector<int>> by_t;
+        for (int k = 0; k < A; ++k) by_t[tgt[act[k]]].push_back(k);
+        const int nt = (int)by_t.size();
+        std::vector<u64 *> tptr, sptr;
+        std::vector<const u64 *> cptr, c0;
+        std::vector<int> seg{0}, item, gj;
+        u64 *sconv = rt.workspace(WS_RELIN_OUT, (size_t)nt * cstride);
+        for (auto &kv : by_t) {
+            tptr.push_back(kv.first);
+            sptr.push_back(sconv + (long long)(tptr.size() - 1) * cstride);
+            for (int k : kv.second) {
+                item.push_back(k);
+                cptr.push_back(kb.conv + (long long)k * cstride);
+                c0.push_back(cur[act[k]]);
+                gj.push_back(g[k]);
+            }
+            seg.push_back((int)item.size());
+        }
+        const int *d_seg = rt.upload_vec(seg);
+        accumulate_seg(ctx, 2, ell, nt, rt.upload_vec(sptr), rt.upload_vec(cptr), d_seg, A, false);
+        LimbMap qm;
+        qm.nl = 2 * ell;
+        for (int b = 0; b < 2; ++b)
+            for (int i = 0; i < ell; ++i) {
+                qm.off[b * ell + i] = b * ell + i;
+                qm.mi[b * ell + i] = i;
+            }
+        FuseArgs fa;
+        fa.ell = ell;
+        fa.K = ctx.K;
+        fa.polys = A;   // sources, for the profiler's byte count
+        fa.acc = kb.acc;
+        fa.acc_stride = kb.acc_stride;
+        fa.pinv = ctx.dt.md_pinv;
+        fa.pinvp = ctx.dt.md_pinv_p;
+        fa.outp = rt.upload_vec(tptr);
+        fa.seg = d_seg;
+        fa.item = rt.upload_vec(item);
+        fa.base = rt.upload_vec(c0);
+        fa.base_g = rt.upload_vec(gj);
+        if (!ntt_forward_fused(ctx, Batch{sconv, cstride, nt, nullptr}, qm, kFuseRotAccum, fa))
+            throw Error(SPFHE_EINVAL, "fused rotate-accumulate transform refused");
+    }
+    // items that need no rotation are added as they are
+    std::map<u64 *, std::vector<int>> plain;
+    for (int i = 0; i < items; ++i)
+        if (plans[i].empty()) plain[tgt[i]].push_back(i);
+    if (!plain.empty()) {
+        std::vector<u64 *> tptr;
+        std::vector<const u64 *> src;
+        std::vector<int> seg{0};
+        for (auto &kv : plain) {
+            tptr.push_back(kv.first);
+            for (int i : kv.second) src.push_back(in[i]);
+            seg.push_back((int)src.size());
+        }
+        accumulate_seg(ctx, 2, ell, (int)tptr.size(), rt.upload_vec(tptr), rt.upload_vec(src), rt.upload_vec(seg),
+                       (int)src.size(), true);
+    }
 }
 
 void rotate_hoisted(Ctx &ctx, const Keys &keys, int ell, const u64 *src, const std::vector<int> &amounts, u64 *out)

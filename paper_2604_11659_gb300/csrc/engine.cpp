@@ -437,14 +437,24 @@ void Engine::run_matches(int ell, const std::vector<int> &ids, const u64 *align,
     // final rotations into target slots, then accumulation per result chunk
     std::vector<const u64 *> zin(m);
     for (int i = 0; i < m; ++i) zin[i] = Z + i * cs2;
-    u64 *W = rt.workspace(WS_MISC, (size_t)m * cs2);
-    rotate_batch(ctx, kk, ell - 2, zin, rf, W, nullptr);
-    std::map<u64 *, std::vector<int>> by_target;
-    for (int i = 0; i < m; ++i) {
-        const MatchTask &t = matches_[order[i]];
-        by_target[t.job->C[t.rc]->d].push_back(i);
+    if (rotate_accumulate_supported(ctx)) {
+        std::vector<u64 *> tg(m);
+        for (int i = 0; i < m; ++i) {
+            const MatchTask &t = matches_[order[i]];
+            tg[i] = t.job->C[t.rc]->d;
+        }
+        rotate_accumulate_batch(ctx, kk, ell - 2, zin, rf, tg, nullptr);
+    } else {
+        u64 *W = rt.workspace(WS_MISC, (size_t)m * cs2);
+        rotate_batch(ctx, kk, ell - 2, zin, rf, W, nullptr);
+        std::map<u64 *, std::vector<int>> by_target;
+        for (int i = 0; i < m; ++i) {
+            const MatchTask &t = matches_[order[i]];
+            by_target[t.job->C[t.rc]->d].push_back(i);
+        }
+        for (auto &kv : by_target)
+            accumulate(ctx, ell - 2, kv.first, W, cs2, rt.upload_vec(kv.second), (int)kv.second.size());
     }
-    for (auto &kv : by_target) accumulate(ctx, ell - 2, kv.first, W, cs2, rt.upload_vec(kv.second), (int)kv.second.size());
     for (int i = 0; i < m; ++i) {
         const MatchTask &t = matches_[order[i]];
         Job *j = t.job;

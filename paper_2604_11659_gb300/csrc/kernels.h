@@ -35,12 +35,21 @@ void ntt_forward(Ctx &ctx, Batch b, const LimbMap &map);
 //     By linearity of the transform this is, residue for residue, ModDown's
 //     output rescaled: the transform of conv and the one of [t]_{q_i} are
 //     taken together.
-enum { kFuseNone = 0, kFuseModDown = 1, kFuseRescale = 2, kFuseRelinRescale = 3 };
+//   kFuseRotAccum (variants 5 and 6 only): the last rotation step of
+//     several key switches summed into their result ciphertexts
+//     (rotate_accumulate_batch): the batch holds, per target t, the sum of
+//     its sources' conv [2][ell][n]; pass B adds
+//     sum_j sigma_{g_j}(c0_j) (polynomial 0) + P^{-1} (sum_j acc_j - X) to
+//     outp[t], j over the sources seg[t] .. seg[t+1]-1 (acc index item[j],
+//     c0 base[j], Galois element base_g[j]).
+enum { kFuseNone = 0, kFuseModDown = 1, kFuseRescale = 2, kFuseRelinRescale = 3, kFuseRotAccum = 4 };
 struct FuseArgs {
     int ell = 0, K = 0, polys = 0, base_c1 = 0;
     const u64 *acc = nullptr;
     const u64 *conv = nullptr;
     long long acc_stride = 0, out_stride = 0, conv_stride = 0;
+    u64 *const *outp = nullptr;
+    const int *seg = nullptr, *item = nullptr;
     const u64 *const *base = nullptr;
     const int *base_g = nullptr;
     u64 *out = nullptr;

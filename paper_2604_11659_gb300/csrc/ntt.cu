@@ -602,6 +602,46 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
                 out[e0 + x] = mul_shoup(sub_mod(y, X, q), inv, invp, q);
             }
         }
+    } else if constexpr (MODE == kFuseRotAccum) {
+        // target it: outp[it] += sum_j sigma_{g_j}(c0_j) (polynomial 0)
+        //                      + P^{-1} (sum_j acc_j - X), X = this transform of
+        // the target's summed conv: the rotated sources' ModDown outputs,
+        // summed (the transform is linear, so one serves them all)
+        const int slot = blockIdx.y, it = blockIdx.z;
+        const int b = slot / f.ell, i = slot % f.ell;
+        const int next = f.ell + f.K;
+        const size_t n = (size_t)1 << log_n;
+        const u64 pinv = __ldg(f.pinv + i), pinvp = __ldg(f.pinvp + i);
+        u64 *__restrict__ out = f.outp[it] + ((size_t)b * f.ell + i) * n;
+        const int j0 = f.seg[it], j1 = f.seg[it + 1];
+        for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
+            u64 sa[8], sc[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sa[r] = sc[r] = 0;
+            for (int j = j0; j < j1; ++j) {
+                const u64 *__restrict__ a = f.acc + (long long)f.item[j] * f.acc_stride + ((size_t)b * next + i) * n;
+                u64 av[8], cv[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) av[r] = a[e0 + x0 + r * r16_step<WL>()];
+                if (b == 0) {
+                    const u64 *__restrict__ c0 = f.base[j] + (size_t)i * n;
+                    const unsigned g = (unsigned)f.base_g[j];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) cv[r] = c0[perm_index((int)(e0 + x0 + r * r16_step<WL>()), g, log_n)];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) sc[r] = add_mod(sc[r], cv[r], q);
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) sa[r] = add_mod(sa[r], av[r], q);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int x = x0 + r * r16_step<WL>();
+                const u64 X = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
+                const u64 v = mul_shoup(sub_mod(sa[r], X, q), pinv, pinvp, q);
+                out[e0 + x] = add_mod(add_mod(v, sc[r], q), out[e0 + x], q);
+            }
+        }
     } else {
         // rescale: out_b[i] = (in_b[i] - [r]_{q_i}) q_t^{-1} ([r]_{q_i} = this transform)
         const int slot = blockIdx.y, it = blockIdx.z;
@@ -828,6 +868,10 @@ template <int P, int V> struct R16FusedV {
             if constexpr (r16_relin_rescale<V>())
                 k_fwd16_b<P, V, kFuseRelinRescale><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
             else throw Error(SPFHE_EINVAL, "no merged relinearise-rescale transform for this NTT variant");
+        } else if (mode == kFuseRotAccum) {
+            if constexpr (r16_relin_rescale<V>())
+                k_fwd16_b<P, V, kFuseRotAccum><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
+            else throw Error(SPFHE_EINVAL, "no fused rotate-accumulate transform for this NTT variant");
         } else k_fwd16_b<P, V, kFuseModDown><<<g, 256, 0, s>>>(a, c.dt.mc, c.dt.tw2, c.log_n, PA, f);
     }
 };
@@ -1028,7 +1072,8 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
 {
     if (ctx.log_n < 12 || ctx.ntt_variant == 1 || ctx.ntt_variant == 2 || b.ids)
         return false;
-    if (mode == kFuseRelinRescale && ctx.ntt_variant != 5 && ctx.ntt_variant != 6) return false;
+    if ((mode == kFuseRelinRescale || mode == kFuseRotAccum) && ctx.ntt_variant != 5 && ctx.ntt_variant != 6)
+        return false;
     launch_checks(b, map);
     if (map.nl <= 0 || b.items <= 0) return true;
     NttArgs a{b.base, b.stride, b.ids, map};
@@ -1052,13 +1097,18 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
         // polynomials, or only c0 for a rotation) and writes out; the rescale
         // reads its input limb and writes out
         const double base_limbs = !f.base ? 0.0 : (f.base_c1 ? 1.0 : 0.5) * map.nl;
-        const double epi = mode == kFuseModDown        ? 16.0 * ctx.n * map.nl + 8.0 * ctx.n * base_limbs
-                           : mode == kFuseRelinRescale ? 24.0 * ctx.n * map.nl
-                                                       : 16.0 * ctx.n * map.nl;
-        prof_end(ctx, t0_, cls, epi * b.items,
+        // rotate-accumulate: per source its acc limbs and (polynomial 0) its
+        // c0 limbs, per target the result read and written
+        const double sources = mode == kFuseRotAccum ? (double)f.polys : 0.0;
+        const double epi = mode == kFuseModDown        ? (16.0 * ctx.n * map.nl + 8.0 * ctx.n * base_limbs) * b.items
+                           : mode == kFuseRelinRescale ? 24.0 * ctx.n * map.nl * b.items
+                           : mode == kFuseRotAccum     ? 8.0 * ctx.n * map.nl * (1.5 * sources + 2.0 * b.items)
+                                                       : 16.0 * ctx.n * map.nl * b.items;
+        prof_end(ctx, t0_, cls, epi,
                  0.5 * ctx.n * PB * map.nl * b.items,
                  mode == kFuseRescale ? "ntt fwd B + rescale final"
-                 : mode == kFuseRelinRescale ? "ntt fwd B + relinearise-rescale final" : "ntt fwd B + moddown final");
+                 : mode == kFuseRelinRescale ? "ntt fwd B + relinearise-rescale final"
+                 : mode == kFuseRotAccum ? "ntt fwd B + rotation sums" : "ntt fwd B + moddown final");
         prof_limbs(ctx, cls, 2, (double)map.nl * b.items);
     }
     return true;

@@ -73,6 +73,17 @@ void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, c
 void rotate_step_batch(Ctx &ctx, int ell, const std::vector<const u64 *> &in, const std::vector<int> &g,
                        const std::vector<const u64 *> &keys, u64 *out);
 
+// Rotation of item i by r[i] through the plan, added into tgt[i]
+// ([2][ell][n], evaluation rep.): bit for bit rotate_batch followed by the
+// sums, with the last step's ModDown transforms taken once per target (see
+// ckks.cpp).  Uses the WS_ROT_*, WS_KS_*, WS_MISC and WS_RELIN_OUT
+// workspaces; needs rotate_accumulate_supported (fused epilogues, n >= 2^12,
+// NTT variant 5 or 6).  Counts the key switches in *ks.
+bool rotate_accumulate_supported(const Ctx &ctx);
+void rotate_accumulate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell,
+                             const std::vector<const u64 *> &in, const std::vector<int> &r,
+                             const std::vector<u64 *> &tgt, uint64_t *ks);
+
 // Full plan rotation of each item by amount r[i] (left, any integer);
 // results in out [items][2][ell][n].  counts the key switches in *ks.
 void rotate_batch(Ctx &ctx, const Keys &keys, int ell, const std::vector<const u64 *> &in,

@@ -139,6 +139,85 @@ bool rotate_accumulate_supported(const Ctx &ctx)
     return ctx.fuse_epilogues && ctx.log_n >= 12 && (ctx.ntt_variant == 5 || ctx.ntt_variant == 6);
 }
 
+// One rotation step of every source (Galois element g[j], key keys[j],
+// sources with equal keys next to each other) added into tgt[j], which holds
+// its initial value.  ModDown's output of source j is
+// sigma_g(c0_j) + P^{-1} (acc_j - NTT(conv_j)); the sources of one target
+// are summed as sum sigma_g(c0_j) + P^{-1} (sum acc_j - NTT(sum conv_j)),
+// the transform being linear over Z_q: one forward transform per target.
+void rotate_step_accumulate(Ctx &ctx, int ell, const std::vector<const u64 *> &in, const std::vector<int> &g,
+                            const std::vector<const u64 *> &keys, const std::vector<u64 *> &tgt)
+{
+    if (!rotate_accumulate_supported(ctx)) throw Error(SPFHE_EINVAL, "fused rotate-accumulate unavailable");
+    const int A = (int)in.size();
+    if (!A) return;
+    Runtime &rt = *ctx.rt;
+    const size_t n = ctx.n;
+    const long long pstride = (long long)ell * n, cstride = 2 * pstride;
+    std::vector<const u64 *> c1(A), tp(A);
+    std::vector<KeyGroup> groups;
+    u64 *tmp = rt.workspace(WS_ROT_TMP, (size_t)A * pstride);
+    for (int k = 0; k < A; ++k) {
+        c1[k] = in[k] + pstride;
+        tp[k] = tmp + k * pstride;
+        if (!groups.empty() && groups.back().key == keys[k])
+            ++groups.back().count;
+        else
+            groups.push_back(KeyGroup{keys[k], k, 1});
+    }
+    automorph(ctx, A, 1, ell, rt.upload_vec(c1), 0, tmp, pstride, rt.upload_vec(g));
+    KsBuffers kb;
+    {
+        InKeySwitch in_ks(ctx);
+        kb = ks_front(ctx, A, ell, rt.upload_vec(tp), groups);
+        moddown_conv(ctx, A, ell, kb.acc, kb.acc_stride, kb.conv);
+    }
+    // sources by target
+    std::map<u64 *, std::vector<int>> by_t;
+    for (int k = 0; k < A; ++k) by_t[tgt[k]].push_back(k);
+    const int nt = (int)by_t.size();
+    std::vector<u64 *> tptr, sptr;
+    std::vector<const u64 *> cptr, c0;
+    std::vector<int> seg{0}, item, gj;
+    u64 *sconv = rt.workspace(WS_ROT_SUM, (size_t)nt * cstride);
+    for (auto &kv : by_t) {
+        tptr.push_back(kv.first);
+        sptr.push_back(sconv + (long long)(tptr.size() - 1) * cstride);
+        for (int k : kv.second) {
+            item.push_back(k);
+            cptr.push_back(kb.conv + (long long)k * cstride);
+            c0.push_back(in[k]);
+            gj.push_back(g[k]);
+        }
+        seg.push_back((int)item.size());
+    }
+    const int *d_seg = rt.upload_vec(seg);
+    accumulate_seg(ctx, 2, ell, nt, rt.upload_vec(sptr), rt.upload_vec(cptr), d_seg, A, false);
+    LimbMap qm;
+    qm.nl = 2 * ell;
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < ell; ++i) {
+            qm.off[b * ell + i] = b * ell + i;
+            qm.mi[b * ell + i] = i;
+        }
+    FuseArgs fa;
+    fa.ell = ell;
+    fa.K = ctx.K;
+    fa.polys = A;   // sources, for the profiler's byte count
+    fa.acc = kb.acc;
+    fa.acc_stride = kb.acc_stride;
+    fa.pinv = ctx.dt.md_pinv;
+    fa.pinvp = ctx.dt.md_pinv_p;
+    fa.outp = rt.upload_vec(tptr);
+    fa.seg = d_seg;
+    fa.item = rt.upload_vec(item);
+    fa.base = rt.upload_vec(c0);
+    fa.base_g = rt.upload_vec(gj);
+    if (!ntt_forward_fused(ctx, Batch{sconv, cstride, nt, nullptr}, qm, kFuseRotAccum, fa))
+        throw Error(SPFHE_EINVAL, "fused rotate-accumulate transform refused");
+}
+
+
 // Rotations through the plan whose results are only summed into result
 // ciphertexts (Alg. 2's EvalRotate then EvalAdd).  Every step but the last
 // runs as in rotate_batch.  The last step's ModDown output is
@@ -210,74 +289,18 @@ void rotate_accumulate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, in
     std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
         return rotation_key(*keys[a], plans[a].back()) < rotation_key(*keys[b], plans[b].back());
     });
-    const int A = (int)act.size();
-    if (A) {
-        std::vector<const u64 *> c1(A), tp(A);
-        std::vector<int> g(A);
-        std::vector<KeyGroup> groups;
-        u64 *tmp = rt.workspace(WS_ROT_TMP, (size_t)A * pstride);
-        for (int k = 0; k < A; ++k) {
-            const int i = act[k];
-            c1[k] = cur[i] + pstride;
-            tp[k] = tmp + k * pstride;
-            g[k] = galois_element(ctx, plans[i].back());
-            const u64 *key = rotation_key(*keys[i], plans[i].back());
-            if (!groups.empty() && groups.back().key == key)
-                ++groups.back().count;
-            else
-                groups.push_back(KeyGroup{key, k, 1});
+    if (!act.empty()) {
+        std::vector<const u64 *> sin, skey;
+        std::vector<int> sg;
+        std::vector<u64 *> st;
+        for (int i : act) {
+            sin.push_back(cur[i]);
+            sg.push_back(galois_element(ctx, plans[i].back()));
+            skey.push_back(rotation_key(*keys[i], plans[i].back()));
+            st.push_back(tgt[i]);
         }
-        automorph(ctx, A, 1, ell, rt.upload_vec(c1), 0, tmp, pstride, rt.upload_vec(g));
-        KsBuffers kb;
-        {
-            InKeySwitch in_ks(ctx);
-            kb = ks_front(ctx, A, ell, rt.upload_vec(tp), groups);
-            moddown_conv(ctx, A, ell, kb.acc, kb.acc_stride, kb.conv);
-        }
-        if (ks) *ks += A;
-        // sources by target
-        std::map<u64 *, std::vector<int>> by_t;
-        for (int k = 0; k < A; ++k) by_t[tgt[act[k]]].push_back(k);
-        const int nt = (int)by_t.size();
-        std::vector<u64 *> tptr, sptr;
-        std::vector<const u64 *> cptr, c0;
-        std::vector<int> seg{0}, item, gj;
-        u64 *sconv = rt.workspace(WS_RELIN_OUT, (size_t)nt * cstride);
-        for (auto &kv : by_t) {
-            tptr.push_back(kv.first);
-            sptr.push_back(sconv + (long long)(tptr.size() - 1) * cstride);
-            for (int k : kv.second) {
-                item.push_back(k);
-                cptr.push_back(kb.conv + (long long)k * cstride);
-                c0.push_back(cur[act[k]]);
-                gj.push_back(g[k]);
-            }
-            seg.push_back((int)item.size());
-        }
-        const int *d_seg = rt.upload_vec(seg);
-        accumulate_seg(ctx, 2, ell, nt, rt.upload_vec(sptr), rt.upload_vec(cptr), d_seg, A, false);
-        LimbMap qm;
-        qm.nl = 2 * ell;
-        for (int b = 0; b < 2; ++b)
-            for (int i = 0; i < ell; ++i) {
-                qm.off[b * ell + i] = b * ell + i;
-                qm.mi[b * ell + i] = i;
-            }
-        FuseArgs fa;
-        fa.ell = ell;
-        fa.K = ctx.K;
-        fa.polys = A;   // sources, for the profiler's byte count
-        fa.acc = kb.acc;
-        fa.acc_stride = kb.acc_stride;
-        fa.pinv = ctx.dt.md_pinv;
-        fa.pinvp = ctx.dt.md_pinv_p;
-        fa.outp = rt.upload_vec(tptr);
-        fa.seg = d_seg;
-        fa.item = rt.upload_vec(item);
-        fa.base = rt.upload_vec(c0);
-        fa.base_g = rt.upload_vec(gj);
-        if (!ntt_forward_fused(ctx, Batch{sconv, cstride, nt, nullptr}, qm, kFuseRotAccum, fa))
-            throw Error(SPFHE_EINVAL, "fused rotate-accumulate transform refused");
+        rotate_step_accumulate(ctx, ell, sin, sg, skey, st);
+        if (ks) *ks += act.size();
     }
     // items that need no rotation are added as they are
     std::map<u64 *, std::vector<int>> plain;

@@ -44,7 +44,8 @@ uint64_t engine_workspace_bound(const Ctx &ctx, int ell)
                            + 2 * (l + K)      // WS_KS_ACC
                            + 2 * l      // WS_KS_CONV
                            + l          // WS_ROT_TMP
-                           + 4 * l;     // WS_ROT_OUT_A, WS_ROT_OUT_B
+                           + 4 * l      // WS_ROT_OUT_A, WS_ROT_OUT_B
+                           + 2 * l;     // WS_ROT_SUM (at most one target per item)
     return (B * limbs + 2 * l) * (uint64_t)ctx.n * sizeof(u64);
 }
 

@@ -123,13 +123,23 @@ class DigitTree {
         if (!merge_) {
             std::vector<int> amt(k);
             for (int i = 0; i < k; ++i) amt[i] = (int)key[i].second;
+            if (rotate_accumulate_supported(ctx_)) {
+                std::vector<u64 *> tg(k);
+                for (int i = 0; i < k; ++i) tg[i] = res_[key[i].first]->d;
+                rotate_accumulate_batch(ctx_, std::vector<const Keys *>(k, &keys_), lv_, ct, amt, tg, &ks);
+                return;
+            }
             rotate_batch(ctx_, keys_, lv_, ct, amt, out, &ks);
             for (int i = 0; i < k; ++i) src[i] = out + (long long)i * cs_;
             add_to_results(key, src);
             return;
         }
-        rotate_digit(key, src, 1, out);
-        route(key, src, 1, 1);
+        if (rotate_accumulate_supported(ctx_)) {
+            rotate_route(key, src, 1, 1);
+        } else {
+            rotate_digit(key, src, 1, out);
+            route(key, src, 1, 1);
+        }
         flush(next, false);
     }
     void finish()
@@ -220,6 +230,72 @@ class DigitTree {
         }
         sum_into(ctx_, 2, lv_, tgt, srcs, fresh);
     }
+    // rotate_digit followed by route with the rotated items' ModDown
+    // transforms taken once per destination sum (rotate_step_accumulate):
+    // items with a zero digit at weight w are summed as they are (starting
+    // fresh sums), fresh sums that receive only rotated items start at zero,
+    // then every rotated item is added into its sum
+    void rotate_route(const std::vector<Key> &key, const std::vector<const u64 *> &src, long long w, int t)
+    {
+        const size_t k = key.size();
+        std::vector<u64 *> dst(k);
+        std::map<u64 *, char> fresh;   // destination -> 1 while it holds nothing yet
+        for (size_t i = 0; i < k; ++i) {
+            const long long rem = key[i].second - digit(key[i].second, w) * w;
+            if (rem == 0) {
+                dst[i] = res_[key[i].first]->d;
+                fresh.emplace(dst[i], 0);
+                continue;
+            }
+            const Key tk{key[i].first, rem};
+            auto it = levels_[t].find(tk);
+            if (it == levels_[t].end()) {
+                dst[i] = levels_[t][tk] = get();
+                fresh[dst[i]] = 1;
+            } else {
+                dst[i] = it->second;
+                fresh.emplace(dst[i], 0);
+            }
+        }
+        // items with a zero digit: plain sums (a fresh sum starts from them)
+        std::map<u64 *, std::vector<const u64 *>> plain;
+        for (size_t i = 0; i < k; ++i)
+            if (!digit(key[i].second, w)) plain[dst[i]].push_back(src[i]);
+        {
+            std::vector<u64 *> tgt;
+            std::vector<std::vector<const u64 *>> srcs;
+            std::vector<char> fr;
+            for (auto &kv : plain) {
+                tgt.push_back(kv.first);
+                srcs.push_back(kv.second);
+                fr.push_back(fresh[kv.first]);
+                fresh[kv.first] = 0;
+            }
+            if (!tgt.empty()) sum_into(ctx_, 2, lv_, tgt, srcs, fr);
+        }
+        for (auto &kv : fresh)
+            if (kv.second)
+                SPFHE_CHECK_CUDA(cudaMemsetAsync(kv.first, 0, (size_t)cs_ * sizeof(u64), ctx_.stream));
+        std::vector<int> rid;
+        for (size_t i = 0; i < k; ++i)
+            if (digit(key[i].second, w)) rid.push_back((int)i);
+        if (rid.empty()) return;
+        // equal keys next to each other for the inner product
+        std::stable_sort(rid.begin(), rid.end(),
+                         [&](int x, int y) { return digit(key[x].second, w) < digit(key[y].second, w); });
+        std::vector<const u64 *> sin, skey;
+        std::vector<int> sg;
+        std::vector<u64 *> st;
+        for (int i : rid) {
+            const int d = digit(key[i].second, w);
+            sin.push_back(src[i]);
+            sg.push_back(galois_element(ctx_, (int)(d * w)));
+            skey.push_back(rotation_key(keys_, (int)(d * w)));
+            st.push_back(dst[i]);
+        }
+        rotate_step_accumulate(ctx_, lv_, sin, sg, skey, st);
+        ks += sin.size();
+    }
     void add_to_results(const std::vector<Key> &key, const std::vector<const u64 *> &src)
     {
         std::map<int, std::vector<const u64 *>> by;
@@ -264,9 +340,13 @@ class DigitTree {
                     src.push_back(levels_[t][k]);
                     levels_[t].erase(k);
                 }
-                u64 *out = ctx_.rt->workspace(WS_TREE_ROT, key.size() * (size_t)cs_);
-                rotate_digit(key, src, w, out);
-                route(key, src, t + 1 < digits_ ? t + 1 : t, w);
+                if (rotate_accumulate_supported(ctx_)) {
+                    rotate_route(key, src, w, t + 1 < digits_ ? t + 1 : t);
+                } else {
+                    u64 *out = ctx_.rt->workspace(WS_TREE_ROT, key.size() * (size_t)cs_);
+                    rotate_digit(key, src, w, out);
+                    route(key, src, t + 1 < digits_ ? t + 1 : t, w);
+                }
                 for (u64 *p : owned) pool_.push_back(p);
             }
         }

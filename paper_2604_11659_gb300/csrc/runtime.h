@@ -50,6 +50,7 @@ enum WsSlot {
     WS_GRP_SUM,
     WS_TREE_ROT,
     WS_HOIST_EXT,
+    WS_ROT_SUM,   // per-target sums of the last rotation step's conversions
 };
 
 // ---- batched evaluator (ckks.cpp) ----
@@ -76,10 +77,15 @@ void rotate_step_batch(Ctx &ctx, int ell, const std::vector<const u64 *> &in, co
 // Rotation of item i by r[i] through the plan, added into tgt[i]
 // ([2][ell][n], evaluation rep.): bit for bit rotate_batch followed by the
 // sums, with the last step's ModDown transforms taken once per target (see
-// ckks.cpp).  Uses the WS_ROT_*, WS_KS_*, WS_MISC and WS_RELIN_OUT
+// ckks.cpp).  Uses the WS_ROT_* (WS_ROT_SUM included), WS_KS_* and WS_MISC
 // workspaces; needs rotate_accumulate_supported (fused epilogues, n >= 2^12,
 // NTT variant 5 or 6).  Counts the key switches in *ks.
 bool rotate_accumulate_supported(const Ctx &ctx);
+// One rotation step per source (Galois element g[j], key keys[j]; equal keys
+// next to each other) added into tgt[j] (which holds its initial value); one
+// forward transform per distinct target (see ckks.cpp).
+void rotate_step_accumulate(Ctx &ctx, int ell, const std::vector<const u64 *> &in, const std::vector<int> &g,
+                            const std::vector<const u64 *> &keys, const std::vector<u64 *> &tgt);
 void rotate_accumulate_batch(Ctx &ctx, const std::vector<const Keys *> &keys, int ell,
                              const std::vector<const u64 *> &in, const std::vector<int> &r,
                              const std::vector<u64 *> &tgt, uint64_t *ks);

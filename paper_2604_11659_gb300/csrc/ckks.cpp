@@ -42,9 +42,12 @@ KsBuffers ks_front(Ctx &ctx, int items, int ell, const u64 *const *d_in, const s
     ctx.prof.ks_bytes += 8.0 * n * (3.0 * ell * items + 2.0 * beta * next * groups.size());
     // ModUp: coefficient representation of every input limb, then one base
     // conversion per digit and forward transforms of the new limbs
-    gather_items(ctx, items, (size_t)coef_stride, d_in, coef, coef_stride);
-    // n^{-1} of this transform is folded into the ModUp conversion's constants
-    ntt_inverse(ctx, Batch{coef, coef_stride, items, nullptr}, limb_range(0, ell, 0), false);
+    // (read straight from the inputs where the transform can; n^{-1} of this
+    // transform is folded into the ModUp conversion's constants)
+    if (!ntt_inverse_from(ctx, Batch{coef, coef_stride, items, nullptr}, d_in, limb_range(0, ell, 0), false)) {
+        gather_items(ctx, items, (size_t)coef_stride, d_in, coef, coef_stride);
+        ntt_inverse(ctx, Batch{coef, coef_stride, items, nullptr}, limb_range(0, ell, 0), false);
+    }
     modup_bconv(ctx, items, ell, coef, coef_stride, ext, ext_stride);
     ntt_forward(ctx, Batch{ext, ext_stride, items, nullptr}, modup_ntt_map(ctx, ell));
     ks_inner_product(ctx, items, ell, d_in, ext, ext_stride, groups, acc, acc_stride);

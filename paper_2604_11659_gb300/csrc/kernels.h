@@ -63,6 +63,11 @@ bool ntt_forward_fused(Ctx &ctx, Batch b, const LimbMap &map, int mode, const Fu
 // below 4q but not reduced (for the key-switching base conversions, whose
 // constants carry the n^{-1} instead)
 void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map, bool scale = true);
+// Out-of-place inverse transform: item z's limbs are read from src[z]
+// (device array of pointers, same limb offsets as `map`) and the result is
+// written to dst.  Radix-16 sizes, no item list and no launch chunking only;
+// returns false otherwise and does nothing.
+bool ntt_inverse_from(Ctx &ctx, Batch dst, const u64 *const *src, const LimbMap &map, bool scale = true);
 LimbMap limb_range(int first_off, int count, int first_mi);
 
 // ---- ring kernels (ring.cu) ----

@@ -37,6 +37,10 @@ struct NttArgs {
     // n x, not reduced below q; for consumers that fold n^{-1} into their own
     // constants, the base conversions of key switching)
     int unscaled = 0;
+    // inverse radix-16 transforms without item list: when set, the first
+    // pass reads item z's limbs from src[z] (same limb offsets) instead of
+    // the batch, which receives the result (an out-of-place transform)
+    const u64 *const *src = nullptr;
 };
 
 __device__ __forceinline__ u64 *limb_ptr(const NttArgs &a, int n, int &mi)
@@ -706,6 +710,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     const int n = 1 << log_n;
     int mi;
     u64 *p = limb_ptr(a, n, mi);
+    const u64 *ps = a.src ? a.src[blockIdx.z] + (long long)a.map.off[blockIdx.y] * n : p;
     const u64 q = mc[mi].q;
     const ulonglong2 *w2 = tw2 + (size_t)mi * n;
     const int tile = threadIdx.x / TPT, t = threadIdx.x % TPT;
@@ -722,7 +727,7 @@ __global__ void __launch_bounds__(256, r16_min_blocks<V>()) k_inv16_b(NttArgs a,
     for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
         u64 tmp[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) tmp[r] = p[e0 + x0 + r * r16_step<WL>()];
+        for (int r = 0; r < 8; ++r) tmp[r] = ps[e0 + x0 + r * r16_step<WL>()];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int x = x0 + r * r16_step<WL>();
@@ -1154,6 +1159,31 @@ void ntt_inverse(Ctx &ctx, Batch b, const LimbMap &map, bool scale)
         prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * b.items, 0.5 * ctx.n * g.PA * map.nl * b.items, "ntt inv A");
         prof_limbs(ctx, cls, 1, (double)map.nl * b.items);
     }
+}
+
+bool ntt_inverse_from(Ctx &ctx, Batch dst, const u64 *const *src, const LimbMap &map, bool scale)
+{
+    if (ctx.log_n < 12 || dst.ids || ctx.ntt_chunk > 0) return false;
+    launch_checks(dst, map);
+    if (map.nl <= 0 || dst.items <= 0) return true;
+    NttArgs a{dst.base, dst.stride, nullptr, map, scale ? 0 : 1, src};
+    NttArgs a2{dst.base, dst.stride, nullptr, map, scale ? 0 : 1};
+    const int cls = ctx.in_keyswitch ? K_KS_NTT_INV : K_NTT_INV;
+    const int PA = pass_a_stages(ctx), PB = ctx.log_n - PA;
+    dim3 grid(ctx.n / kElems, map.nl, dst.items);
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        r16_dispatch(PB, [&](auto L) { decltype(L)::inv_b(grid, ctx.stream, a, ctx, PA); });
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * dst.items, 0.5 * ctx.n * PB * map.nl * dst.items, "ntt inv B");
+        prof_limbs(ctx, cls, 0, (double)map.nl * dst.items);
+    }
+    {
+        cudaEvent_t t0_ = prof_begin(ctx);
+        r16_dispatch(PA, [&](auto L) { decltype(L)::inv_a(grid, ctx.stream, a2, ctx); });
+        prof_end(ctx, t0_, cls, 8.0 * ctx.n * map.nl * dst.items, 0.5 * ctx.n * PA * map.nl * dst.items, "ntt inv A");
+        prof_limbs(ctx, cls, 1, (double)map.nl * dst.items);
+    }
+    return true;
 }
 
 }  // namespace spfhe

@@ -79,7 +79,8 @@ bool relin_rescale_supported(const Ctx &ctx, int ell)
 // t_b = P^{-1} (INTT(acc_b[t]) - conv_b[t]) + INTT(base_b[t]) comes from two
 // inverse transforms of top limbs instead of one.
 void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
-                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride)
+                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride, const u64 *const *mask,
+                         const int *mask_g)
 {
     if (items <= 0) return;
     if (!relin_rescale_supported(ctx, ell)) throw Error(SPFHE_EINVAL, "merged relinearise-rescale unavailable");
@@ -132,6 +133,8 @@ void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, c
     fa.qt_mod = ctx.dt.rs_qt + (size_t)(ell - 1) * ctx.L;
     fa.inv = ctx.dt.rs_inv + (size_t)(ell - 1) * ctx.L;
     fa.invp = ctx.dt.rs_inv_p + (size_t)(ell - 1) * ctx.L;
+    fa.mask = mask;
+    fa.mask_g = mask_g;
     if (!ntt_forward_fused(ctx, Batch{spread, 2LL * (ell - 1) * (long long)n, items, nullptr}, sm, kFuseRelinRescale,
                            fa))
         throw Error(SPFHE_EINVAL, "merged relinearise-rescale transform refused");

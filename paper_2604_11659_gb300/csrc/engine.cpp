@@ -427,12 +427,14 @@ void Engine::run_matches(int ell, const std::vector<int> &ids, const u64 *align,
             groups.push_back(KeyGroup{key, i, 1});
     }
     if (relin_rescale_supported(ctx, ell)) {
-        relin_rescale_batch(ctx, m, ell, rt.upload_vec(d2), groups, rt.upload_vec(dbase), T, Y, cs1);
+        // the mask product rides on the rescale's last pass
+        relin_rescale_batch(ctx, m, ell, rt.upload_vec(d2), groups, rt.upload_vec(dbase), T, Y, cs1,
+                            rt.upload_vec(mk), rt.upload_vec(gm));
     } else {
         keyswitch_batch(ctx, m, ell, rt.upload_vec(d2), groups, rt.upload_vec(dbase), nullptr, true, X, csL);
         rescale(ctx, m, ell, rt.upload_vec(x1), T, Y, cs1);
+        mul_plain_perm(ctx, m, ell - 1, Y, cs1, rt.upload_vec(mk), rt.upload_vec(gm));
     }
-    mul_plain_perm(ctx, m, ell - 1, Y, cs1, rt.upload_vec(mk), rt.upload_vec(gm));
     // Relinearize after a plaintext product has nothing to switch
     rescale(ctx, m, ell - 1, rt.upload_vec(x2), T, Z, cs2);
     // final rotations into target slots, then accumulation per result chunk

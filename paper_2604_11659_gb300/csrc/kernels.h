@@ -50,6 +50,10 @@ struct FuseArgs {
     long long acc_stride = 0, out_stride = 0, conv_stride = 0;
     u64 *const *outp = nullptr;
     const int *seg = nullptr, *item = nullptr;
+    // kFuseRelinRescale: optional per-item mask (Montgomery form, [ell-1][n],
+    // read through sigma_{mask_g}) multiplied into the rescaled output
+    const u64 *const *mask = nullptr;
+    const int *mask_g = nullptr;
     const u64 *const *base = nullptr;
     const int *base_g = nullptr;
     u64 *out = nullptr;

@@ -590,6 +590,10 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
         const u64 *__restrict__ acc = f.acc + it * f.acc_stride + ((size_t)b * next + i) * ((size_t)1 << log_n);
         const u64 *__restrict__ base = f.base[it] + ((size_t)b * f.ell + i) * ((size_t)1 << log_n);
         u64 *__restrict__ out = f.out + it * f.out_stride + ((size_t)b * (f.ell - 1) + i) * ((size_t)1 << log_n);
+        // optional mask product (Alg. 2's mask multiply after this rescale):
+        // the Montgomery-form mask limb read through sigma_{mask_g}
+        const u64 *__restrict__ mk = f.mask ? f.mask[it] + ((size_t)i << log_n) : nullptr;
+        const unsigned mg = f.mask ? (unsigned)f.mask_g[it] : 1u;
         for (int x0 = r16_first<WL>(); x0 < r16_end<WL>(); x0 += 8 * r16_step<WL>()) {
             u64 av[8], bv[8];
 #pragma unroll
@@ -603,7 +607,9 @@ __device__ __forceinline__ void fwd16_b_body(u64 *sm, u64 *p, const ModConst &m,
                 const int x = x0 + r * r16_step<WL>();
                 const u64 X = reduce_any(sm[r16_slot_b<P>(x >> P, x & ((1 << P) - 1))], q, m.one_p);
                 const u64 y = add_mod(mul_shoup(av[r], pinv, pinvp, q), bv[r], q);
-                out[e0 + x] = mul_shoup(sub_mod(y, X, q), inv, invp, q);
+                u64 v = mul_shoup(sub_mod(y, X, q), inv, invp, q);
+                if (mk) v = redc(mul_wide(v, mk[perm_index((int)(e0 + x), mg, log_n)]), q, m.qneg_inv);
+                out[e0 + x] = v;
             }
         }
     } else if constexpr (MODE == kFuseRotAccum) {

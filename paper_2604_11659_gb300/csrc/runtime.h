@@ -66,8 +66,12 @@ void keyswitch_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const
 // rescale's; see ckks.cpp).  tmp holds items * 2 * ell * n words.  Needs
 // relin_rescale_supported (fused epilogues, n >= 2^12, NTT variant 5 or 6).
 bool relin_rescale_supported(const Ctx &ctx, int ell);
+// mask / mask_g (device arrays, or nullptr): the rescaled output is also
+// multiplied by mask[item] (Montgomery form, [ell-1][n]) read through
+// sigma_{mask_g[item]}, as mul_plain_perm would afterwards.
 void relin_rescale_batch(Ctx &ctx, int items, int ell, const u64 *const *d_in, const std::vector<KeyGroup> &groups,
-                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride);
+                         const u64 *const *d_base, u64 *tmp, u64 *out, long long out_stride,
+                         const u64 *const *mask = nullptr, const int *mask_g = nullptr);
 
 // One rotation step per item: item i of `in` ([2][ell][n]) rotated with
 // Galois element g[i] and key keys[i]; out [items][2][ell][n].

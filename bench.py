@@ -234,7 +234,7 @@ def tune_ntt(sp, ctx, rec, chunk, variant=0):
     if chunk >= 0:
         set_ntt(sp, ctx, (variant, 0, chunk))
         return (variant, 0, chunk), None
-    items = 32 if rec.log_n >= 15 else 64
+    items = 64
     splits = [pa for pa in range(6, 10) if 6 <= rec.log_n - pa <= 9] if rec.log_n >= 12 else [0]
     best, timings = None, {}
     for var in (0, 1, 2, 3, 4, 5, 6):

@@ -123,7 +123,7 @@ spfhe_status spfhe_ctx_moduli(const spfhe_ctx *ctx, uint64_t *mods, uint64_t *ps
 spfhe_status spfhe_sync(spfhe_ctx *ctx);
 
 /* Matches per batch of the encrypted products (and alignment rotations per
- * wave): 1 .. 1024, or 0 for the default (32 at n >= 2^15, else 64).  Larger
+ * wave): 1 .. 1024, or 0 for the default (64).  Larger
  * batches share each relinearisation key stream over more matches and need
  * about 320 MB of batch buffers per match at n = 2^16, L = 24. */
 spfhe_status spfhe_ctx_set_match_batch(spfhe_ctx *ctx, uint32_t matches);

@@ -19,7 +19,7 @@ static int env_int(const char *name, int dflt)
 int match_batch_size(const Ctx &ctx)
 {
     if (ctx.match_batch > 0) return ctx.match_batch;
-    const int dflt = ctx.n >= (1 << 15) ? 32 : 64;
+    const int dflt = 64;   // measured at n = 2^16: 64 matches 2 % faster than 32, 48 in between
     return std::max(1, std::min(env_int("SPFHE_MATCH_BATCH", dflt), 1024));
 }
 

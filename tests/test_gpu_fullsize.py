@@ -89,8 +89,8 @@ def test_bench_workload_decrypts_within_tolerance():
 
 def test_bench_ring_launch_configurations_bit_identical():
     """At the benchmark's ring with the library's own keys, a 128x128 product
-    with a few hundred matches (several 32-match batches and a ragged last
-    one) yields bit-identical result ciphertexts whatever the match batch (32,
+    with a few hundred matches (464: seven 64-match batches and a ragged last
+    one) yields bit-identical result ciphertexts whatever the match batch (64,
     the default; 7; 1, one match per launch sequence), the NTT kernel variant
     (6, the default; 5; 0) and the epilogue fusion.  Every launch computes the
     same integers by construction; this checks it at full size in the
@@ -114,7 +114,7 @@ def test_bench_ring_launch_configurations_bit_identical():
 
     try:
         outs, ref, st = run()
-        assert st["matches"] > 3 * 32 and st["matches"] % 32 != 0
+        assert st["matches"] > 3 * 64 and st["matches"] % 64 != 0
         assert g.check(outs) < 1e-4
         g.free(outs)
         settings = [("match batch 7", lambda on: sp.spfhe_ctx_set_match_batch(g.ctx, 7 if on else 0)),

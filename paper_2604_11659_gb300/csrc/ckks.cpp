@@ -223,7 +223,6 @@ void rotate_step_accumulate(Ctx &ctx, int ell, const std::vector<const u64 *> &i
         throw Error(SPFHE_EINVAL, "fused rotate-accumulate transform refused");
 }
 
-
 // Rotations through the plan whose results are only summed into result
 // ciphertexts (Alg. 2's EvalRotate then EvalAdd).  Every step but the last
 // runs as in rotate_batch.  The last step's ModDown output is
